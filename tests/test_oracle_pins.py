@@ -1,0 +1,367 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a limit, brute force over explicit indices or over determinants, a
+library routine, or an invariance.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import make_problem
+from fockspace import TinySystem, so
+
+
+# ---------------------------------------------------------------- regularizer
+def test_regularizer_against_high_precision():
+    """Eq. A7 regularizer, both branches, against 50-digit arithmetic."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    s = 0.5
+    deltas = [-7.3, -2.0, -0.8, -0.2, -0.05, -0.044, -0.0447, -1e-3, -1e-6, -1e-12,
+              1e-9, 0.02, 0.0447213, 0.3, 1.7]
+    for c in (1.0, 2.0):
+        got = O.regularizer(np.array(deltas), s, c)
+        for d, g in zip(deltas, got):
+            ref = (1 - mp.exp(-c * s * mp.mpf(d) ** 2)) / mp.mpf(d)
+            assert abs(g - float(ref)) <= 4e-16 * abs(float(ref)), (d, c, g, ref)
+    assert O.regularizer(np.array([0.0]), s)[0] == 0.0
+    assert np.all(O.regularizer(np.array([-1.0, 0.5]), 0.0) == 0.0)
+
+
+# ------------------------------------------------------- single-reference limit
+@pytest.fixture(scope="module")
+def sr_problem():
+    return make_problem(ncore=4, nact=0, nvir=9, naux=17, seed=5, s=0.5)
+
+
+def _so_integrals(prob):
+    """Antisymmetrised spin-orbital <ij||ab> for a closed-shell SR problem,
+    built by explicit loops from the DF factors."""
+    nc, nv = prob.ncore, prob.nvir
+    B = prob.B
+    g = np.zeros((2 * nc, 2 * nc, 2 * nv, 2 * nv))
+    for I, J, A, Bb in itertools.product(range(2 * nc), range(2 * nc), range(2 * nv), range(2 * nv)):
+        i, si = divmod(I, 2)
+        j, sj = divmod(J, 2)
+        a, sa = divmod(A, 2)
+        b, sb = divmod(Bb, 2)
+        direct = sum(B[q, i, a] * B[q, j, b] for q in range(B.shape[0])) if (si == sa and sj == sb) else 0.0
+        exch = sum(B[q, i, b] * B[q, j, a] for q in range(B.shape[0])) if (si == sb and sj == sa) else 0.0
+        g[I, J, A, Bb] = direct - exch
+    return g
+
+
+def test_sr_large_s_is_mp2(sr_problem):
+    """s -> infinity: E_vv -> closed-shell MP2, D_vv -> MP2 unrelaxed vv density
+    (the single-reference statement after Eq. A12).  MP2 is evaluated in the
+    spin-orbital textbook form: E = 1/4 sum <ij||ab>^2/D, P_ab = 1/2 sum t_ac t_bc."""
+    prob = sr_problem
+    prob_inf = make_problem(ncore=4, nact=0, nvir=9, naux=17, seed=5, s=1.0e4)
+    g = _so_integrals(prob)
+    nc, nv = prob.ncore, prob.nvir
+    e = np.repeat(prob.eps[:nc], 2)
+    ev = np.repeat(prob.eps[nc:], 2)
+    D = e[:, None, None, None] + e[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    t = g / D
+    emp2 = 0.25 * np.sum(g * t)
+    pab = 0.5 * np.einsum("ijac,ijbc->ab", t, t)
+    p_sf = pab[0::2, 0::2] + pab[1::2, 1::2]
+    assert abs(O.e_vv(prob_inf) - emp2) <= 1e-12 * abs(emp2)
+    d = O.dvv(prob_inf)
+    assert np.max(np.abs(d - p_sf)) <= 1e-12 * np.max(np.abs(p_sf))
+    # at finite s the energy is strictly smaller in magnitude
+    assert abs(O.e_vv(prob)) < abs(emp2)
+
+
+def test_sr_small_s_limit(sr_problem):
+    """s -> 0: R2 = 2 s Delta + O(s^2), so E_vv / s -> 2 sum nu (2 nu - nu_swap) Delta;
+    D_vv = O(s^2); at s = 0 everything vanishes."""
+    base = dict(ncore=4, nact=0, nvir=9, naux=17, seed=5)
+    p0 = make_problem(s=0.0, **base)
+    assert O.e_vv(p0) == 0.0
+    assert np.all(O.dvv(p0) == 0.0)
+    nc, nv = 4, 9
+    lin = 0.0
+    for m in range(nc):
+        for n in range(nc):
+            nu = p0.B[:, m, :].T @ p0.B[:, n, :]
+            nus = p0.B[:, n, :].T @ p0.B[:, m, :]      # nu^{nm}_{ef} = (en|fm)
+            d = p0.eps[m] + p0.eps[n] - p0.eps[nc:][:, None] - p0.eps[nc:][None, :]
+            lin += np.sum(nu * (2 * nu - nus) * 2.0 * d)
+    for s in (1e-4, 1e-5):
+        ps = make_problem(s=s, **base)
+        assert abs(O.e_vv(ps) / s - lin) <= 2.0 * s * 60.0 * abs(lin)
+        d2 = O.dvv(ps)
+        ps2 = make_problem(s=2 * s, **base)
+        ratio = np.linalg.norm(O.dvv(ps2)) / np.linalg.norm(d2)
+        # D ~ s^2 (1 + O(s Delta^2)); Delta^2 <= 60 here
+        assert abs(ratio - 4.0) < 4.0 * 2.0 * s * 60.0
+
+
+# ----------------------------------------------------------- 4-index brute force
+def test_four_index_brute_force_energy():
+    """E_vv from explicitly formed (ai|bj) integrals and index loops."""
+    prob = make_problem(ncore=2, nact=2, nvir=3, naux=5, seed=8, nstates=2, s=0.6)
+    nc, na, nv = 2, 2, 3
+    nh = nc + na
+    B = prob.B
+    I4 = np.zeros((nh, na + nv, nh, na + nv))
+    for i, a, j, b in itertools.product(range(nh), range(na + nv), range(nh), range(na + nv)):
+        I4[i, a, j, b] = sum(B[q, i, a] * B[q, j, b] for q in range(B.shape[0]))
+    g1h = np.zeros((nh, nh))
+    g1h[:nc, :nc] = 2 * np.eye(nc)
+    g1h[nc:, nc:] = prob.gamma1
+    lam = np.zeros((nh,) * 4)
+    lam[nc:, nc:, nc:, nc:] = prob.lambda2
+    eps = prob.eps
+    ep = eps[nc:]
+    e = 0.0
+    for k, l, i, j in itertools.product(range(nh), repeat=4):
+        g2 = lam[k, l, i, j] + g1h[k, i] * g1h[l, j] - 0.5 * g1h[l, i] * g1h[k, j]
+        if g2 == 0.0:
+            continue
+        for a, b in itertools.product(range(na, na + nv), repeat=2):
+            dij = eps[i] + eps[j] - ep[a] - ep[b]
+            dkl = eps[k] + eps[l] - ep[a] - ep[b]
+            rij = (1 - np.exp(-prob.s * dij * dij)) / dij
+            rkl = (1 - np.exp(-prob.s * dkl * dkl)) / dkl
+            tij = I4[i, a, j, b] * rij
+            tkl = I4[k, a, l, b] * rkl
+            e += 0.5 * g2 * tij * (2 * I4[k, a, l, b] - dij * tkl)
+    assert abs(O.e_vv(prob) - e) <= 1e-13 * abs(e)
+
+
+# ----------------------------------------------------- Fock-space brute force
+def _full_t2(prob, ts):
+    nc, na, nv = prob.ncore, prob.nact, prob.nvir
+    nh, npart = nc + na, na + nv
+    t2 = np.zeros((nh, nh, npart, npart))
+    for i in range(nh):
+        for j in range(nh):
+            t2[i, j, na:, na:] = O.t2_vv(prob, i, j)[0]
+            if na:
+                t2[i, j, na:, :na] = ts[i, j]
+                t2[i, j, :na, na:] = ts[j, i].T
+    return t2
+
+
+@pytest.mark.parametrize("nel_act,weights,seed", [(2, (0.6, 0.4), 7), (4, (0.3, 0.7), 3)])
+def test_fock_space_dvv_energy_and_t1(nel_act, weights, seed):
+    """Eq. A12 terms 1-12 (+ the Lambda3 term 13, formed here from the CI),
+    E_vv, and the one-body part of [H0, T2] in Eq. A6, all against explicit
+    determinant-space evaluation with spin-adapted (singlet) ensembles."""
+    nc, na, nv = 2, 3, 2
+    sysm = TinySystem(nc, na, nv, nel_act=nel_act, nstates=2, seed=seed, weights=weights)
+    prob = make_problem(nc, na, nv, 6, seed=11 + seed, nstates=1, s=0.7)
+    prob.gamma1, prob.lambda2 = sysm.gamma1, sysm.lambda2
+    nh, npart = nc + na, na + nv
+    ts = O.t2_semi_internal(prob)
+    t1 = O.t1_amplitudes(prob, ts)
+    t2 = _full_t2(prob, ts)
+    t1f = np.zeros((nh, npart))
+    t1f[:, na:] = t1
+    T = sysm.cluster(t1f, t2)
+    brute = sysm.dvv(T - T.T)
+    terms = O.dvv_terms(prob, ts=ts, t1=t1)
+    taa = ts[nc:, nc:]
+    t13 = np.einsum("uwez,xyfv,xyzuvw->ef", taa, taa, sysm.lambda3)
+    d = sum(terms.values()) + t13
+    scale = np.max(np.abs(brute))
+    assert np.max(np.abs(d - brute)) <= 1e-12 * scale
+    # each amplitude class separately (no cross-class contraction survives)
+    t2vv = np.zeros_like(t2)
+    t2vv[:, :, na:, na:] = t2[:, :, na:, na:]
+    Tv = sysm.cluster(None, t2vv)
+    assert np.allclose(sysm.dvv(Tv - Tv.T), terms[4] + terms[5] + terms[7], rtol=0, atol=1e-12 * scale)
+    # E_vv
+    nu_vv = np.zeros((nh, nh, nv, nv))
+    for k in range(nh):
+        for l in range(nh):
+            nu_vv[k, l] = O.nu_pair(prob, k, l, slice(na, None), slice(na, None))
+    H0 = sysm.h0(prob.eps)
+    eb = sysm.energy(sysm.v_vv(nu_vv), H0, Tv - Tv.T)
+    assert abs(O.e_vv(prob) - eb) <= 1e-12 * abs(eb)
+    # Eq. A6: one-body part of [H0, T2] for core -> virtual
+    T2 = sysm.cluster(None, t2)
+    X = H0 @ T2 - T2 @ H0
+    base = nc + na
+    eh, ep = O.hole_eps(prob), O.particle_eps(prob)
+    R = O.regularizer(eh[:nc, None] - ep[na:][None, :], prob.s)
+    ref = t1[:nc] / R
+    for m in range(nc):
+        for e in range(nv):
+            op = sysm.fs.e1(so(m, 0), so(base + e, 0))
+            y = sysm.expect(lambda psi: op @ (X @ psi))
+            assert abs(y - ref[m, e]) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_fock_space_sr_number_conservation():
+    """Single reference: the trace of the core block of Gamma^(2) (brute force)
+    cancels the trace of the oracle's D_vv; the vv block is PSD."""
+    nc, na, nv = 2, 0, 3
+    sysm = TinySystem(nc, 1, nv, nel_act=0, nstates=1, seed=1)
+    prob = make_problem(nc, 1, nv, 7, seed=2, nstates=1, s=0.9)
+    # no active electrons: the single active orbital is empty; drop its amplitudes
+    prob.gamma1 = np.zeros((1, 1))
+    prob.lambda2 = np.zeros((1, 1, 1, 1))
+    nh, npart = nc + 1, 1 + nv
+    t2 = np.zeros((nh, nh, npart, npart))
+    for m in range(nc):
+        for n in range(nc):
+            t2[m, n, 1:, 1:] = O.t2_vv(prob, m, n)[0]
+    T = sysm.cluster(None, t2)
+    A = T - T.T
+    occ = 0.0
+    for m in range(nc):
+        E = sum(sysm.fs.e1(so(m, s), so(m, s)) for s in (0, 1))
+        occ += 0.5 * sysm.expect(lambda psi: E @ (A @ (A @ psi)) - 2 * (A @ (E @ (A @ psi)))
+                                  + A @ (A @ (E @ psi)))
+    d = O.dvv_terms(prob, terms=(4,))[4]
+    assert abs(np.trace(d) + occ) <= 1e-12 * abs(occ)
+    assert np.min(np.linalg.eigvalsh(0.5 * (d + d.T))) > -1e-15
+
+
+# ---------------------------------------------------------- structural pins
+def test_vv_terms_match_hole_rdm_form():
+    """Terms 4 + 5 + 7 equal 1/2 sum Gamma2_H[k][l][i][j] (tau^{kl} tau^{ij T}
+    + tau^{kl T} tau^{ij}), the form the vv block takes when the particle
+    pair is virtual (derived like E_vv)."""
+    prob = make_problem(ncore=3, nact=3, nvir=7, naux=11, seed=4, nstates=3, s=0.5)
+    terms = O.dvv_terms(prob, terms=(4, 5, 7))
+    g2h = O.gamma2_holes(prob)
+    nh = 6
+    tau = {(i, j): O.t2_vv(prob, i, j)[0] for i in range(nh) for j in range(nh)}
+    d = np.zeros((7, 7))
+    for k, l, i, j in itertools.product(range(nh), repeat=4):
+        w = g2h[k, l, i, j]
+        if w:
+            d += 0.5 * w * (tau[(k, l)] @ tau[(i, j)].T + tau[(k, l)].T @ tau[(i, j)])
+    ref = terms[4] + terms[5] + terms[7]
+    assert np.max(np.abs(d - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_dvv_symmetric_and_invariant_under_aux_rotation():
+    prob = make_problem(ncore=3, nact=2, nvir=6, naux=9, seed=12, nstates=2, s=0.5)
+    d, asym = O.dvv(prob, return_asym=True)
+    assert asym <= 1e-12 * np.linalg.norm(d)
+    q, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((9, 9)))
+    p2 = make_problem(ncore=3, nact=2, nvir=6, naux=9, seed=12, nstates=2, s=0.5)
+    p2.B = np.einsum("PQ,Qhp->Php", q, prob.B)
+    assert abs(O.e_vv(p2) - O.e_vv(prob)) <= 1e-12 * abs(O.e_vv(prob))
+    assert np.max(np.abs(O.dvv(p2) - d)) <= 1e-12 * np.max(np.abs(d))
+
+
+def test_dvv_covariant_under_virtual_permutation_and_sign():
+    prob = make_problem(ncore=2, nact=2, nvir=5, naux=8, seed=13, nstates=2, s=0.5)
+    d = O.dvv(prob)
+    perm = np.array([3, 0, 4, 1, 2])
+    sign = np.array([1, -1, 1, 1, -1.0])
+    p2 = make_problem(ncore=2, nact=2, nvir=5, naux=8, seed=13, nstates=2, s=0.5)
+    na = 2
+    p2.B = prob.B.copy()
+    p2.B[:, :, na:] = prob.B[:, :, na:][:, :, perm] * sign[None, None, :]
+    p2.eps = prob.eps.copy()
+    p2.eps[4:] = prob.eps[4:][perm]
+    d2 = O.dvv(p2)
+    ref = d[np.ix_(perm, perm)] * np.outer(sign, sign)
+    assert np.max(np.abs(d2 - ref)) <= 1e-13 * np.max(np.abs(d))
+    assert abs(np.trace(d2) - np.trace(d)) <= 1e-13 * abs(np.trace(d))
+
+
+def test_dvv_rotation_inside_degenerate_block():
+    """Two virtuals with equal energies: rotating them rotates D_vv."""
+    prob = make_problem(ncore=2, nact=0, nvir=4, naux=7, seed=14, s=0.5)
+    prob.eps[3] = prob.eps[2]
+    d = O.dvv(prob)
+    th = 0.37
+    U = np.eye(4)
+    U[0:2, 0:2] = [[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]]
+    p2 = make_problem(ncore=2, nact=0, nvir=4, naux=7, seed=14, s=0.5)
+    p2.eps = prob.eps.copy()
+    p2.B = np.einsum("Qhe,ef->Qhf", prob.B, U)
+    assert np.max(np.abs(O.dvv(p2) - U.T @ d @ U)) <= 1e-13 * np.max(np.abs(d))
+
+
+# ------------------------------------------------------------ eigen / truncate
+def test_natural_orbitals_against_lapack():
+    prob = make_problem(ncore=3, nact=2, nvir=12, naux=20, seed=15, nstates=2, s=0.5)
+    d = O.dvv(prob)
+    n, v = O.natural_orbitals(d)
+    assert np.all(np.diff(n) <= 0)
+    assert np.linalg.norm(d @ v - v * n) <= 1e-12 * np.linalg.norm(d)
+    assert np.linalg.norm(v.T @ v - np.eye(12)) <= 1e-13
+    ref = np.sort(np.linalg.eigvals(d).real)[::-1]
+    assert np.max(np.abs(ref - n)) <= 1e-14 * np.max(np.abs(n)) * 10
+
+
+@pytest.mark.parametrize("ons,mode,thr,expect", [
+    ([4.0, 3.0, 2.0, 1.0], 0, 70.0, 2),         # cum 0.7 reached exactly at k = 2
+    ([4.0, 3.0, 2.0, 1.0], 0, 70.0001, 3),
+    ([4.0, 3.0, 2.0, 1.0], 0, 100.0, 4),
+    ([4.0, 3.0, 2.0, 1.0], 0, 0.0, 1),
+    ([4.0, 3.0, 2.0, 1.0], 1, 50.0, 2),
+    ([4.0, 3.0, 2.0, 1.0], 1, 51.0, 3),
+    ([4.0, 3.0, 2.0, 1.0], 2, 2.0, 3),
+    ([4.0, 3.0, 2.0, 1.0], 2, 5.0, 0),
+    ([1.0, 0.995, 0.9852, 0.5], 0, 30.0, 3),    # widening chain 1 -> 2 -> 3
+    ([1.0, 0.99, 0.5, 0.49], 0, 30.0, 1),       # 0.01 difference is not < 0.01
+    ([1.0, 0.5, 0.496, -1e-6], 0, 85.0, 3),     # negative ON in the denominator
+])
+def test_truncation_rules(ons, mode, thr, expect):
+    assert O.truncate(np.array(ons), mode, thr, 0.01) == expect
+
+
+def test_correction_limits():
+    prob = make_problem(ncore=3, nact=2, nvir=10, naux=14, seed=16, nstates=2, s=0.5)
+    d = O.dvv(prob)
+    n, v = O.natural_orbitals(d)
+    e = O.e_vv(prob)
+    de, efno, _ = O.discarded_correction(prob, v, 10, e)
+    assert abs(de) <= 1e-12 * abs(e)
+    de0, _, _ = O.discarded_correction(prob, v, 0, e)
+    assert de0 == e
+    de5, efno5, eps5 = O.discarded_correction(prob, v, 5, e)
+    assert np.all(np.diff(eps5) >= 0)
+    assert abs(efno5) < abs(e)
+
+
+# ------------------------------------------------------------- generator RDMs
+def test_generator_rdms_against_fock_space():
+    """synth.ci spin-free RDMs of a random CI vector agree with the
+    determinant-space helper's spin-orbital RDMs summed over spin."""
+    from synth import ci
+    from fockspace import FockSpace, gamma1_spin_orbital, rdm_spin_orbital
+    rng = np.random.default_rng(3)
+    norb = 4
+    vecs, sa, ta, tb = ci.random_ci_vectors(rng, norb, 1)
+    g1, g2 = ci.spin_free_rdms(vecs[0], norb, ta, tb)
+    fs = FockSpace(norb, norb)
+    psi = np.zeros(fs.dim)
+    for ia, a in enumerate(sa):
+        for ib, b in enumerate(sa):
+            d = 0
+            for p in range(norb):
+                if (int(a) >> p) & 1:
+                    d |= 1 << so(p, 0)
+                if (int(b) >> p) & 1:
+                    d |= 1 << so(p, 1)
+            # determinant order: alpha creators first, then beta; the Fock
+            # space orders creators by spin orbital index (interleaved).
+            occ_a = [so(p, 0) for p in range(norb) if (int(a) >> p) & 1]
+            occ_b = [so(p, 1) for p in range(norb) if (int(b) >> p) & 1]
+            seq = occ_a + occ_b
+            inv = sum(1 for x in range(len(seq)) for y in range(x + 1, len(seq)) if seq[x] > seq[y])
+            psi[fs.index[d]] = vecs[0][ia, ib] * (-1) ** inv
+    w = [1.0]
+    so_all = list(range(2 * norb))
+    G1 = gamma1_spin_orbital(fs, [psi], w)
+    G2 = rdm_spin_orbital(fs, [psi], w, so_all, 2)
+    g1_ref = G1[0::2, 0::2] + G1[1::2, 1::2]
+    g2_ref = np.einsum("uavbxayb->uvxy", G2.reshape((norb, 2) * 4))
+    assert np.max(np.abs(g1 - g1_ref)) < 1e-13
+    assert np.max(np.abs(g2 - g2_ref)) < 1e-13
+    assert abs(np.trace(g1) - norb) < 1e-13
+    assert abs(np.einsum("pqpq->", g2) - norb * (norb - 1)) < 1e-12
