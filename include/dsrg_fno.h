@@ -1,0 +1,134 @@
+/*
+ * dsrg_fno.h - C ABI of the GB300 (sm_103a) FNO SA-DSRG-PT2 hot path.
+ *
+ * Method: frozen natural orbitals for state-averaged DSRG, arXiv:2312.07008.
+ * The library forms the regularised first-order amplitudes of SA-DSRG-PT2
+ * from density-fitted integrals (Eqs. A6, A7), contracts them into the
+ * virtual-virtual block of the unrelaxed second-order 1-RDM (Eq. A12) and the
+ * vv-class second-order energy (scalar of Eq. A4), diagonalises that block
+ * into natural orbitals (Eq. 8), truncates the virtual NOs (Eqs. 9, 10 and
+ * the near-degeneracy rule of Sec. 2), and forms the second-order correction
+ * for the discarded virtuals (scalar part of Eq. 11).
+ *
+ * Conventions shared by every entry point
+ *   - nh = ncore + nact holes (core first), np = nact + nvir particles
+ *     (active first).  Orbitals are semicanonical.
+ *   - Arrays are row-major, float64, caller-owned.  "device" pointers are
+ *     CUDA device memory of the current device, 8-byte aligned; "host"
+ *     pointers are ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; scalars returned through host
+ *     pointers are valid when the call returns (the call synchronises the
+ *     stream for them).
+ *   - Return value: DSRG_FNO_OK (0) or a negative dsrg_fno_status.  On error
+ *     the outputs are unspecified.  No C++ exception crosses the ABI.
+ *   - The library keeps a grow-only device workspace per device; it is freed
+ *     by dsrg_fno_release().  Calls on one device are serialised by the
+ *     library's workspace lock; one problem per call.
+ */
+#ifndef DSRG_FNO_H
+#define DSRG_FNO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DSRG_FNO_OK = 0,
+  DSRG_FNO_ERR_ARG = -1,        /* invalid argument (null pointer, size, mode) */
+  DSRG_FNO_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  DSRG_FNO_ERR_NOMEM = -3,      /* device workspace could not be allocated */
+  DSRG_FNO_ERR_NOCONV = -4,     /* the eigensolver did not converge */
+  DSRG_FNO_ERR_TIMEOUT = -5,    /* a bounded device wait expired */
+  DSRG_FNO_ERR_NONFINITE = -6,  /* an input or result is NaN/Inf */
+  DSRG_FNO_ERR_UNSUPPORTED = -7 /* valid request this build does not serve */
+} dsrg_fno_status;
+
+/* Arithmetic of the integral contractions.  FP64: plain float64 on the CUDA
+ * cores.  SLICED_BF16: each float64 row is split into `nslices` exact bfloat16
+ * digit planes with a per-row power-of-two scale; digit products run on the
+ * tensor cores (tcgen05) with exact float32 partial sums and float64
+ * accumulation (regulariser, energy, D_vv accumulation and eigensolve stay
+ * float64). */
+typedef enum { DSRG_FNO_FP64 = 0, DSRG_FNO_SLICED_BF16 = 1 } dsrg_fno_precision;
+
+typedef struct {
+  int32_t ncore, nact, nvir, naux;
+  /* device [naux][nh][np]: B^Q_{ip}, hole i, particle p (DF factors, Sec. 3);
+   * the active(hole) x active(particle) sub-block must be symmetric in (i,p). */
+  const double* B_hp;
+  /* device [ncore+nact+nvir]: semicanonical orbital energies eps_p, ordered
+   * core | active | virtual (the Delta denominators below Eq. A7). */
+  const double* eps;
+  /* device [nact][nact]: state-averaged spin-free 1-RDM Gamma^u_v (Eq. A1);
+   * NULL iff nact == 0. */
+  const double* gamma1;
+  /* device [nact]^4: state-averaged spin-free 2-cumulant Lambda^{uv}_{xy},
+   * with Gamma^{uv}_{xy} = Lambda + Gamma^u_x Gamma^v_y - 1/2 Gamma^v_x Gamma^u_y
+   * (definitions after Eq. A12); NULL iff nact == 0. */
+  const double* lambda2;
+  /* device [nh][np] off-diagonal Fock f^i_a of Eq. A6, or NULL (= 0). */
+  const double* f_hp;
+  /* host [nstates] state weights w_alpha of Eq. A1: each >= 0, sum 1 (1e-12).
+   * Metadata: the densities above already carry them. */
+  int32_t nstates;
+  const double* weights;
+  /* flow parameter s (E_h^-2), s >= 0 (Eq. A7). */
+  double s;
+  int32_t precision;  /* dsrg_fno_precision */
+  int32_t nslices;    /* SLICED_BF16 digit planes (2..8); 0 = library default */
+} dsrg_fno_problem;
+
+/* vv-class SA-DSRG-PT2 energy E_vv (doubles whose particles are both
+ * virtual; Eq. A4 scalar restricted to them; in the single-reference limit
+ * the whole DSRG-PT2 energy).  e2_out: host scalar. */
+int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stream);
+
+/* D_vv = virtual-virtual block of the unrelaxed PT2 1-RDM correction, Eq. A12
+ * terms 1-12 (the Lambda3 term 13 is not formed, as Sec. 2 allows when the
+ * energy drops Lambda3), symmetrised.  dvv_out: device [nvir][nvir].
+ * e2_out: host, may be NULL; when given, receives E_vv of the same pass. */
+int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
+                     void* stream);
+
+/* Natural orbitals of D_vv (Eq. 8) and the truncation of Sec. 2.
+ *   dvv       device [nvir][nvir], symmetric, read only.
+ *   mode      0: p_o (Eq. 10, threshold in percent of the summed ONs);
+ *             1: p_v (Eq. 9, threshold in percent of nvir, rounded up);
+ *             2: n_kappa (keep ONs >= threshold).
+ *   degen_ratio  near-degeneracy widening: while the next ON differs from the
+ *             last kept one by less than degen_ratio times the larger, keep it
+ *             (0.01 in the paper); 0 disables.
+ *   on_out    device [nvir]: ONs, descending.
+ *   no_out    device [nvir][nvir]: column k is the NO of on_out[k] in the
+ *             semicanonical virtual basis; sign: largest |component| > 0.
+ *   nkept_out host: N'.  */
+int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double threshold,
+                      double degen_ratio, double* on_out, double* no_out,
+                      int32_t* nkept_out, void* stream);
+
+/* Second-order correction for the discarded virtuals (scalar part of
+ * Eq. 11): the kept NOs (first nkept columns of `no`, device [nvir][nvir])
+ * are recanonicalised (virtual Fock block diagonal, Sec. 2), B is rotated to
+ * them, and E_vv is re-evaluated in that basis.
+ *   e2_mo_in    host or NULL: E_vv(MO) of the same problem (as returned by
+ *               dsrg_fno_vv_opdm); NULL makes the call evaluate it.
+ *   de_out      host: E_vv(MO) - E_vv(FNO).
+ *   e2_fno_out  host or NULL: E_vv(FNO).
+ *   eps_fno_out device [nkept] or NULL: recanonicalised virtual energies, ascending. */
+int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept,
+                                  const double* no, const double* e2_mo_in, double* de_out,
+                                  double* e2_fno_out, double* eps_fno_out, void* stream);
+
+/* Human-readable text of a status code. */
+const char* dsrg_fno_status_string(int status);
+
+/* Frees the device workspace of every device the library touched. */
+void dsrg_fno_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSRG_FNO_H */

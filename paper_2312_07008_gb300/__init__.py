@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) FNO SA-DSRG-PT2 hot path (arXiv:2312.07008).
+
+The computation lives in libdsrg_fno.so (hand-written CUDA behind a C ABI,
+include/dsrg_fno.h); this package is its thin ctypes binding.
+"""
+from .binding import (  # noqa: F401
+    FP64, SLICED_BF16, MODE_PO, MODE_PV, MODE_NKAPPA, DsrgFnoError, Problem, problem_from_synth,
+    dsrg_fno_pt2_energy, dsrg_fno_vv_opdm, dsrg_fno_truncate, dsrg_fno_discarded_correction,
+    dsrg_fno_release, load, LIB_PATH, EXPORTED,
+)

@@ -1,0 +1,148 @@
+"""ctypes binding of libdsrg_fno.so: argument marshalling only.
+
+The functions carry the names of the C ABI (include/dsrg_fno.h).  Device
+arrays are torch tensors (float64, contiguous, on the current CUDA device);
+every step of the computation runs in the library's CUDA kernels.  A missing
+library raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdsrg_fno.so")
+
+EXPORTED = (
+    "dsrg_fno_pt2_energy",
+    "dsrg_fno_vv_opdm",
+    "dsrg_fno_truncate",
+    "dsrg_fno_discarded_correction",
+    "dsrg_fno_status_string",
+    "dsrg_fno_release",
+)
+
+FP64 = 0
+SLICED_BF16 = 1
+MODE_PO, MODE_PV, MODE_NKAPPA = 0, 1, 2
+
+
+class DsrgFnoError(RuntimeError):
+    def __init__(self, func: str, status: int, text: str):
+        super().__init__(f"{func} returned {status}: {text}")
+        self.status = status
+
+
+class CProblem(ctypes.Structure):
+    _fields_ = [
+        ("ncore", ctypes.c_int32), ("nact", ctypes.c_int32), ("nvir", ctypes.c_int32), ("naux", ctypes.c_int32),
+        ("B_hp", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("gamma1", ctypes.c_void_p),
+        ("lambda2", ctypes.c_void_p), ("f_hp", ctypes.c_void_p),
+        ("nstates", ctypes.c_int32), ("weights", ctypes.POINTER(ctypes.c_double)),
+        ("s", ctypes.c_double), ("precision", ctypes.c_int32), ("nslices", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(path)
+    vp, d, i32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32
+    P = ctypes.POINTER(CProblem)
+    lib.dsrg_fno_pt2_energy.argtypes = [P, ctypes.POINTER(d), vp]
+    lib.dsrg_fno_vv_opdm.argtypes = [P, vp, ctypes.POINTER(d), vp]
+    lib.dsrg_fno_truncate.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
+    lib.dsrg_fno_discarded_correction.argtypes = [P, i32, vp, ctypes.POINTER(d), ctypes.POINTER(d),
+                                                  ctypes.POINTER(d), vp, vp]
+    lib.dsrg_fno_status_string.argtypes = [ctypes.c_int]
+    lib.dsrg_fno_status_string.restype = ctypes.c_char_p
+    lib.dsrg_fno_release.argtypes = []
+    for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_truncate", "dsrg_fno_discarded_correction"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(func: str, status: int):
+    if status != 0:
+        raise DsrgFnoError(func, status, load().dsrg_fno_status_string(status).decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+class Problem:
+    """Holds the C struct and keeps its tensors alive."""
+
+    def __init__(self, ncore, nact, nvir, naux, B, eps, gamma1=None, lambda2=None, f_hp=None,
+                 weights=(1.0,), s=0.5, precision=FP64, nslices=0):
+        self.tensors = (B, eps, gamma1, lambda2, f_hp)
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+        self._w = w
+        self.c = CProblem(ncore, nact, nvir, naux, _ptr(B), _ptr(eps), _ptr(gamma1), _ptr(lambda2), _ptr(f_hp),
+                          len(w), w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(s), int(precision),
+                          int(nslices))
+        self.ncore, self.nact, self.nvir, self.naux = ncore, nact, nvir, naux
+
+
+def problem_from_synth(p, device="cuda", precision=FP64, nslices=0):
+    """Uploads a synth.Problem (numpy) to the device and wraps it."""
+    import torch
+    t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)  # noqa: E731
+    return Problem(p.ncore, p.nact, p.nvir, p.naux, t(p.B), t(p.eps), t(p.gamma1), t(p.lambda2), t(p.f_hp),
+                   p.weights, p.s, precision, nslices)
+
+
+def dsrg_fno_pt2_energy(prob: Problem, stream=None) -> float:
+    e = ctypes.c_double()
+    _check("dsrg_fno_pt2_energy", load().dsrg_fno_pt2_energy(ctypes.byref(prob.c), ctypes.byref(e), _stream(stream)))
+    return e.value
+
+
+def dsrg_fno_vv_opdm(prob: Problem, dvv_out, stream=None) -> float:
+    e = ctypes.c_double()
+    _check("dsrg_fno_vv_opdm", load().dsrg_fno_vv_opdm(ctypes.byref(prob.c), _ptr(dvv_out), ctypes.byref(e),
+                                                      _stream(stream)))
+    return e.value
+
+
+def dsrg_fno_truncate(nvir, dvv, mode, threshold, degen_ratio, on_out, no_out, stream=None) -> int:
+    k = ctypes.c_int32()
+    _check("dsrg_fno_truncate", load().dsrg_fno_truncate(nvir, _ptr(dvv), mode, float(threshold),
+                                                        float(degen_ratio), _ptr(on_out), _ptr(no_out),
+                                                        ctypes.byref(k), _stream(stream)))
+    return k.value
+
+
+def dsrg_fno_discarded_correction(prob: Problem, nkept, no, e2_mo=None, eps_fno_out=None, stream=None):
+    de, ef = ctypes.c_double(), ctypes.c_double()
+    emo = None if e2_mo is None else ctypes.byref(ctypes.c_double(e2_mo))
+    _check("dsrg_fno_discarded_correction",
+           load().dsrg_fno_discarded_correction(ctypes.byref(prob.c), int(nkept), _ptr(no), emo, ctypes.byref(de),
+                                                ctypes.byref(ef), _ptr(eps_fno_out), _stream(stream)))
+    return de.value, ef.value
+
+
+def dsrg_fno_release():
+    load().dsrg_fno_release()

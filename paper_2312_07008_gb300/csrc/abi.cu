@@ -1,0 +1,520 @@
+// C ABI of the FNO SA-DSRG-PT2 library: argument checks, the batch plan over
+// hole-pair groups, workspace management and the order of the kernels.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kernels.h"
+
+namespace dsrg {
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+static std::mutex g_ws_mutex;
+static Workspace g_ws[64];
+
+std::mutex& workspace_mutex() { return g_ws_mutex; }
+
+Workspace& workspace_for_current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  g_ws[dev].device = dev;
+  return g_ws[dev];
+}
+
+int ws_reserve(Workspace& ws, size_t bytes) {
+  ws.off = 0;
+  if (bytes <= ws.cap) return DSRG_FNO_OK;
+  if (ws.base) {
+    DSRG_CUDA(cudaDeviceSynchronize());
+    DSRG_CUDA(cudaFree(ws.base));
+    ws.base = nullptr;
+    ws.cap = 0;
+  }
+  if (cudaMalloc(&ws.base, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ws.base = nullptr;
+    return DSRG_FNO_ERR_NOMEM;
+  }
+  ws.cap = bytes;
+  return DSRG_FNO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batch plan: hole-pair groups closed under the coupling of the hole 2-RDM
+// ---------------------------------------------------------------------------
+struct Batch {
+  int pair_begin, npairs, desc_begin, ndesc;
+};
+
+struct Plan {
+  std::vector<int2> pairs;
+  std::vector<DressDesc> desc;
+  std::vector<Batch> batches;
+  int max_pairs = 0, max_desc = 0;
+};
+
+static void build_plan(int nc, int na, long cap_pairs, Plan& P) {
+  struct Group {
+    std::vector<int2> pairs;
+    std::vector<DressDesc> desc;  // slot/out relative to the group
+  };
+  std::vector<Group> groups;
+  for (int m = 0; m < nc; ++m)
+    for (int n = m; n < nc; ++n) {
+      Group G;
+      G.pairs.push_back(make_int2(m, n));
+      if (m == n) G.desc.push_back({DRESS_CC_DIAG, 0, 0, 0, 0});
+      else {
+        G.desc.push_back({DRESS_CC_SYM, 0, 0, 0, 0});
+        G.desc.push_back({DRESS_CC_ANTI, 0, 0, 0, 0});
+      }
+      groups.push_back(G);
+    }
+  if (na > 0) {
+    for (int m = 0; m < nc; ++m) {
+      Group G;
+      for (int u = 0; u < na; ++u) G.pairs.push_back(make_int2(m, nc + u));
+      for (int k = 0; k < na; ++k) {
+        G.desc.push_back({DRESS_CA_SYM, 0, k, m, 0});
+        G.desc.push_back({DRESS_CA_ANTI, 0, k, m, 0});
+      }
+      groups.push_back(G);
+    }
+    Group G;
+    for (int u = 0; u < na; ++u)
+      for (int v = u; v < na; ++v) G.pairs.push_back(make_int2(nc + u, nc + v));
+    const int ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
+    for (int k = 0; k < ns; ++k) G.desc.push_back({DRESS_AA_SYM, 0, k, 0, 0});
+    for (int k = 0; k < nd; ++k) G.desc.push_back({DRESS_AA_ANTI, 0, k, 0, 0});
+    groups.push_back(G);
+  }
+  long largest = 0;
+  for (auto& G : groups) largest = std::max<long>(largest, (long)G.pairs.size());
+  cap_pairs = std::max(cap_pairs, largest);
+  Batch cur{0, 0, 0, 0};
+  for (auto& G : groups) {
+    if (cur.npairs > 0 && cur.npairs + (long)G.pairs.size() > cap_pairs) {
+      P.batches.push_back(cur);
+      cur = Batch{(int)P.pairs.size(), 0, (int)P.desc.size(), 0};
+    }
+    for (auto d : G.desc) {
+      d.slot += cur.npairs;
+      d.out = cur.ndesc++;
+      P.desc.push_back(d);
+    }
+    for (auto p : G.pairs) P.pairs.push_back(p);
+    cur.npairs += (int)G.pairs.size();
+  }
+  if (cur.npairs > 0) P.batches.push_back(cur);
+  for (auto& b : P.batches) {
+    P.max_pairs = std::max(P.max_pairs, b.npairs);
+    P.max_desc = std::max(P.max_desc, b.ndesc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Argument checks
+// ---------------------------------------------------------------------------
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int validate(const dsrg_fno_problem* p) {
+  if (!p) return DSRG_FNO_ERR_ARG;
+  if (p->ncore < 0 || p->nact < 0 || p->nvir < 0 || p->naux < 0) return DSRG_FNO_ERR_ARG;
+  if (p->nact > 16) return DSRG_FNO_ERR_UNSUPPORTED;
+  if (p->ncore + p->nact == 0 || p->nvir == 0) return DSRG_FNO_ERR_ARG;
+  if (!(p->s >= 0.0) || !isfinite(p->s)) return DSRG_FNO_ERR_ARG;
+  if (p->precision != DSRG_FNO_FP64 && p->precision != DSRG_FNO_SLICED_BF16) return DSRG_FNO_ERR_ARG;
+  if (p->precision == DSRG_FNO_SLICED_BF16) return DSRG_FNO_ERR_UNSUPPORTED;
+  if (p->naux > 0 && !is_device_ptr(p->B_hp)) return DSRG_FNO_ERR_ARG;
+  if (!is_device_ptr(p->eps)) return DSRG_FNO_ERR_ARG;
+  if (p->nact > 0 && (!is_device_ptr(p->gamma1) || !is_device_ptr(p->lambda2))) return DSRG_FNO_ERR_ARG;
+  if (p->f_hp && !is_device_ptr(p->f_hp)) return DSRG_FNO_ERR_ARG;
+  if (p->nstates > 0) {
+    if (!p->weights) return DSRG_FNO_ERR_ARG;
+    double s = 0.0;
+    for (int k = 0; k < p->nstates; ++k) {
+      if (!(p->weights[k] >= 0.0)) return DSRG_FNO_ERR_ARG;
+      s += p->weights[k];
+    }
+    if (fabs(s - 1.0) > 1e-12) return DSRG_FNO_ERR_ARG;
+  }
+  return DSRG_FNO_OK;
+}
+
+static int check_inputs_finite(const dsrg_fno_problem* p, int* flag, cudaStream_t st) {
+  const long nh = p->ncore + p->nact, np = p->nact + p->nvir;
+  DSRG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  DSRG_TRY(check_finite(p->B_hp, (long)p->naux * nh * np, flag, st));
+  DSRG_TRY(check_finite(p->eps, nh + p->nvir, flag, st));
+  if (p->nact) {
+    DSRG_TRY(check_finite(p->gamma1, (long)p->nact * p->nact, flag, st));
+    DSRG_TRY(check_finite(p->lambda2, (long)p->nact * p->nact * p->nact * p->nact, flag, st));
+  }
+  if (p->f_hp) DSRG_TRY(check_finite(p->f_hp, nh * np, flag, st));
+  int h = 0;
+  DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  return h ? DSRG_FNO_ERR_NONFINITE : DSRG_FNO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One pass over the hole pairs: E_vv and, with want_d, the vv classes of D.
+// ---------------------------------------------------------------------------
+struct PassBuffers {
+  int2* pairs;
+  DressDesc* desc;
+  double *tau, *kap, *sig, *sig_sign, *e_part, *dpart, *ts, *e_acc;
+  double *g1A, *g1V, *g1W, *MsA, *MsV, *MsW, *MaA, *MaV, *MaW;
+  int* status;
+  int nsplit;
+};
+
+static size_t doubles(size_t n) { return ws_bytes(n, sizeof(double)); }
+
+static long pair_cap_for_budget(int nv, size_t budget) {
+  const double per_pair = 4.0 * (double)nv * nv * 8.0 + 1024.0;
+  long cap = (long)(budget / per_pair);
+  return std::max<long>(cap, 1);
+}
+
+static size_t device_budget() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return (size_t)4 << 30;
+  }
+  size_t b = (size_t)(0.45 * (double)fr);
+  return std::min(b, (size_t)48 << 30);
+}
+
+static int run_pass(const Geometry& g, const double* B, const double* eps, const double* gamma1,
+                    const double* lambda2, const Plan& P, PassBuffers& W, bool want_d, double* D,
+                    cudaStream_t st) {
+  const int na = g.na;
+  DressAux aux{};
+  if (na > 0) {
+    const int ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
+    DSRG_CUDA(cudaMemcpyAsync(W.g1A, gamma1, sizeof(double) * na * na, cudaMemcpyDeviceToDevice, st));
+    DSRG_TRY(eig_sym_jacobi(na, W.g1A, W.g1V, W.g1W, W.status, 60, st));
+    DSRG_TRY(aa_blocks(na, gamma1, lambda2, W.MsA, W.MaA, st));
+    DSRG_TRY(eig_sym_jacobi(ns, W.MsA, W.MsV, W.MsW, W.status, 60, st));
+    if (nd > 0) DSRG_TRY(eig_sym_jacobi(nd, W.MaA, W.MaV, W.MaW, W.status, 60, st));
+    aux.g1_evec = W.g1V;
+    aux.g1_eval = W.g1A;
+    aux.aas_evec = W.MsV;
+    aux.aas_eval = W.MsA;
+    aux.aaa_evec = W.MaV;
+    aux.aaa_eval = W.MaA;
+  }
+  const int ntd = ceil_div(g.nv, 32);
+  for (size_t bi = 0; bi < P.batches.size(); ++bi) {
+    const Batch& b = P.batches[bi];
+    DSRG_TRY(pair_gemm_f64(g, B, eps, W.pairs + b.pair_begin, b.npairs, W.tau, W.kap, want_d ? W.ts : nullptr,
+                           st));
+    DSRG_TRY(dress_f64(g, W.desc + b.desc_begin, b.ndesc, aux, W.tau, W.kap, W.sig, W.sig_sign, W.e_part, want_d,
+                       st));
+    DSRG_TRY(ordered_sum(W.e_part, (long)b.ndesc * ntd * ntd, W.e_acc, bi > 0, st));
+    if (want_d) DSRG_TRY(syrk_dressed_f64(g.nv, b.ndesc, W.sig, W.sig_sign, W.dpart, W.nsplit, D, st));
+  }
+  if (P.batches.empty()) DSRG_CUDA(cudaMemsetAsync(W.e_acc, 0, sizeof(double), st));
+  return DSRG_FNO_OK;
+}
+
+static int nsplit_for(int nv, int ndesc) {
+  const int nt = ceil_div(nv, 64);
+  const int tiles = nt * (nt + 1) / 2;
+  int ns = ceil_div(2L * 152, tiles);
+  ns = std::min(ns, std::max(ndesc, 1));
+  return std::max(ns, 1);
+}
+
+// Carves the pass buffers out of the workspace (sizes must match pass_bytes).
+static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nsplit) {
+  const size_t nv2 = (size_t)g.nv * g.nv;
+  const int na = g.na, ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
+  const int ntd = ceil_div(g.nv, 32);
+  size_t b = 0;
+  b += ws_bytes(P.pairs.size(), sizeof(int2));
+  b += ws_bytes(P.desc.size(), sizeof(DressDesc));
+  b += 2 * doubles((size_t)P.max_pairs * nv2);
+  b += doubles(want_d ? (size_t)P.max_desc * nv2 : 1);
+  b += doubles((size_t)P.max_desc + 1);
+  b += doubles((size_t)P.max_desc * ntd * ntd + 1);
+  b += doubles(want_d ? (size_t)nsplit * nv2 : 1);
+  b += doubles(want_d && na ? (size_t)g.nh * g.nh * g.nv * na : 1);
+  b += doubles(8);
+  b += 3 * doubles((size_t)na * na + 1) + doubles(2 * (size_t)na * na + 8);
+  b += 2 * doubles((size_t)ns * ns + 1) + doubles(2 * (size_t)ns * ns + 8);
+  b += 2 * doubles((size_t)nd * nd + 1) + doubles(2 * (size_t)nd * nd + 8);
+  b += ws_bytes(8, sizeof(int));
+  return b;
+}
+
+static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want_d, int nsplit, PassBuffers& W,
+                      cudaStream_t st) {
+  const size_t nv2 = (size_t)g.nv * g.nv;
+  const int na = g.na, ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
+  const int ntd = ceil_div(g.nv, 32);
+  W.pairs = ws_take<int2>(ws, P.pairs.size());
+  W.desc = ws_take<DressDesc>(ws, P.desc.size());
+  W.tau = ws_take<double>(ws, (size_t)P.max_pairs * nv2);
+  W.kap = ws_take<double>(ws, (size_t)P.max_pairs * nv2);
+  W.sig = ws_take<double>(ws, want_d ? (size_t)P.max_desc * nv2 : 1);
+  W.sig_sign = ws_take<double>(ws, (size_t)P.max_desc + 1);
+  W.e_part = ws_take<double>(ws, (size_t)P.max_desc * ntd * ntd + 1);
+  W.dpart = ws_take<double>(ws, want_d ? (size_t)nsplit * nv2 : 1);
+  W.ts = ws_take<double>(ws, want_d && na ? (size_t)g.nh * g.nh * g.nv * na : 1);
+  W.e_acc = ws_take<double>(ws, 8);
+  W.g1A = ws_take<double>(ws, (size_t)na * na + 1);
+  W.g1V = ws_take<double>(ws, (size_t)na * na + 1);
+  W.g1W = ws_take<double>(ws, 2 * (size_t)na * na + 8);
+  (void)ws_take<double>(ws, (size_t)na * na + 1);
+  W.MsA = ws_take<double>(ws, (size_t)ns * ns + 1);
+  W.MsV = ws_take<double>(ws, (size_t)ns * ns + 1);
+  W.MsW = ws_take<double>(ws, 2 * (size_t)ns * ns + 8);
+  W.MaA = ws_take<double>(ws, (size_t)nd * nd + 1);
+  W.MaV = ws_take<double>(ws, (size_t)nd * nd + 1);
+  W.MaW = ws_take<double>(ws, 2 * (size_t)nd * nd + 8);
+  W.status = ws_take<int>(ws, 8);
+  W.nsplit = nsplit;
+  if (!W.status) return DSRG_FNO_ERR_NOMEM;
+  if (!P.pairs.empty())
+    DSRG_CUDA(cudaMemcpyAsync(W.pairs, P.pairs.data(), P.pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  if (!P.desc.empty())
+    DSRG_CUDA(cudaMemcpyAsync(W.desc, P.desc.data(), P.desc.size() * sizeof(DressDesc), cudaMemcpyHostToDevice,
+                              st));
+  return DSRG_FNO_OK;
+}
+
+static Geometry geometry_of(const dsrg_fno_problem* p) {
+  Geometry g;
+  g.nc = p->ncore;
+  g.na = p->nact;
+  g.nv = p->nvir;
+  g.nq = p->naux;
+  g.nh = p->ncore + p->nact;
+  g.np = p->nact + p->nvir;
+  g.s = p->s;
+  return g;
+}
+
+// Energy-only pass for an arbitrary geometry (used for the MO and FNO bases).
+static int energy_pass(const Geometry& g, const double* B, const double* eps, const double* gamma1,
+                       const double* lambda2, Workspace& ws, size_t base_off, double* e_out, cudaStream_t st) {
+  Plan P;
+  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, device_budget()), P);
+  ws.off = base_off;
+  PassBuffers W{};
+  size_t need = base_off + pass_bytes(g, P, false, 1);
+  if (need > ws.cap) return DSRG_FNO_ERR_NOMEM;
+  DSRG_TRY(carve_pass(ws, g, P, false, 1, W, st));
+  DSRG_TRY(run_pass(g, B, eps, gamma1, lambda2, P, W, false, nullptr, st));
+  DSRG_CUDA(cudaMemcpyAsync(e_out, W.e_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  return DSRG_FNO_OK;
+}
+
+static size_t energy_pass_bytes(const Geometry& g) {
+  Plan P;
+  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, device_budget()), P);
+  return pass_bytes(g, P, false, 1);
+}
+
+}  // namespace dsrg
+
+using namespace dsrg;
+
+extern "C" {
+
+const char* dsrg_fno_status_string(int s) {
+  switch (s) {
+    case DSRG_FNO_OK: return "ok";
+    case DSRG_FNO_ERR_ARG: return "invalid argument";
+    case DSRG_FNO_ERR_CUDA: return "CUDA runtime error";
+    case DSRG_FNO_ERR_NOMEM: return "device workspace allocation failed";
+    case DSRG_FNO_ERR_NOCONV: return "eigensolver did not converge";
+    case DSRG_FNO_ERR_TIMEOUT: return "bounded device wait expired";
+    case DSRG_FNO_ERR_NONFINITE: return "non-finite input or result";
+    case DSRG_FNO_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+void dsrg_fno_release(void) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < 64; ++d) {
+    if (g_ws[d].base) {
+      cudaSetDevice(d);
+      cudaDeviceSynchronize();
+      cudaFree(g_ws[d].base);
+      g_ws[d].base = nullptr;
+      g_ws[d].cap = 0;
+      g_ws[d].off = 0;
+    }
+  }
+  cudaSetDevice(cur);
+}
+
+int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stream) {
+  int s = validate(prob);
+  if (s) return s;
+  if (!e2_out) return DSRG_FNO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  const Geometry g = geometry_of(prob);
+  DSRG_TRY(ws_reserve(ws, energy_pass_bytes(g) + ws_bytes(8, sizeof(int))));
+  int* flag = ws_take<int>(ws, 8);
+  DSRG_TRY(check_inputs_finite(prob, flag, st));
+  return energy_pass(g, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, ws.off, e2_out, st);
+}
+
+int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out, void* stream) {
+  int s = validate(prob);
+  if (s) return s;
+  if (!dvv_out || !is_device_ptr(dvv_out)) return DSRG_FNO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  const Geometry g = geometry_of(prob);
+  Plan P;
+  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, device_budget()), P);
+  const int nsplit = nsplit_for(g.nv, P.max_desc);
+  const size_t small = small_terms_work_doubles(g.nc, g.na, g.nv);
+  size_t need = ws_bytes(8, sizeof(int)) + pass_bytes(g, P, true, nsplit) + doubles((size_t)g.nh * g.nv) +
+                doubles(small + 1);
+  DSRG_TRY(ws_reserve(ws, need));
+  int* flag = ws_take<int>(ws, 8);
+  DSRG_TRY(check_inputs_finite(prob, flag, st));
+  PassBuffers W{};
+  DSRG_TRY(carve_pass(ws, g, P, true, nsplit, W, st));
+  double* t1 = ws_take<double>(ws, (size_t)g.nh * g.nv);
+  double* work = ws_take<double>(ws, small + 1);
+  const size_t nv2 = (size_t)g.nv * g.nv;
+  DSRG_CUDA(cudaMemsetAsync(dvv_out, 0, nv2 * sizeof(double), st));
+  DSRG_TRY(run_pass(g, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, P, W, true, dvv_out, st));
+  if (g.na > 0 || prob->f_hp) {
+    DSRG_TRY(t1_amplitudes(g, g.na ? W.ts : nullptr, prob->eps, prob->f_hp, prob->gamma1, t1, st));
+    DSRG_TRY(small_terms_f64(g, g.na ? W.ts : nullptr, t1, prob->gamma1, prob->lambda2, dvv_out, work, st));
+  }
+  DSRG_TRY(symmetrize(g.nv, dvv_out, st));
+  DSRG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  DSRG_TRY(check_finite(dvv_out, (long)nv2, flag, st));
+  double e = 0.0;
+  int h = 0;
+  DSRG_CUDA(cudaMemcpyAsync(&e, W.e_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  if (h || !isfinite(e)) return DSRG_FNO_ERR_NONFINITE;
+  if (e2_out) *e2_out = e;
+  return DSRG_FNO_OK;
+}
+
+int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,
+                      double* on_out, double* no_out, int32_t* nkept_out, void* stream) {
+  if (nvir <= 0 || !dvv || !on_out || !no_out || !nkept_out) return DSRG_FNO_ERR_ARG;
+  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  if (!is_device_ptr(dvv) || !is_device_ptr(on_out) || !is_device_ptr(no_out)) return DSRG_FNO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  const size_t n2 = (size_t)nvir * nvir;
+  DSRG_TRY(ws_reserve(ws, 2 * doubles(n2) + doubles(2 * n2 + 8) + ws_bytes(nvir + 8, sizeof(int))));
+  double* A = ws_take<double>(ws, n2);
+  double* V = ws_take<double>(ws, n2);
+  double* work = ws_take<double>(ws, 2 * n2 + 8);
+  int* ib = ws_take<int>(ws, nvir + 8);
+  int* status = ib;
+  int* nk = ib + 1;
+  int* rank = ib + 8;
+  DSRG_CUDA(cudaMemcpyAsync(A, dvv, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  int s = eig_sym_jacobi(nvir, A, V, work, status, 60, st);
+  if (s) return s;
+  DSRG_TRY(eig_sort(nvir, A, V, on_out, no_out, rank, true, true, st));
+  DSRG_TRY(truncate_ons(nvir, on_out, mode, threshold, degen_ratio, nk, st));
+  int h = 0;
+  DSRG_CUDA(cudaMemcpyAsync(&h, nk, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  *nkept_out = h;
+  return DSRG_FNO_OK;
+}
+
+int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, const double* no,
+                                  const double* e2_mo_in, double* de_out, double* e2_fno_out,
+                                  double* eps_fno_out, void* stream) {
+  int s = validate(prob);
+  if (s) return s;
+  if (!de_out || !no || nkept < 0 || nkept > prob->nvir || !is_device_ptr(no)) return DSRG_FNO_ERR_ARG;
+  if (eps_fno_out && !is_device_ptr(eps_fno_out)) return DSRG_FNO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  const Geometry g = geometry_of(prob);
+  Geometry gf = g;
+  gf.nv = nkept;
+  gf.np = g.na + nkept;
+  const int nk = nkept, nv = g.nv;
+  const size_t nk2 = (size_t)nk * nk;
+  const long rows = (long)g.nq * g.nh;
+  size_t fixed = ws_bytes(8, sizeof(int)) + doubles((size_t)nv * nk) * 2 + doubles(nk2) * 3 + doubles(2 * nk2 + 8) +
+                 ws_bytes(nk + 8, sizeof(int)) + doubles((size_t)rows * gf.np + 1) + doubles(g.nh + nk + 1) +
+                 doubles(nk + 1);
+  size_t pass_mo = e2_mo_in ? 0 : energy_pass_bytes(g);
+  size_t pass_f = nk > 0 ? energy_pass_bytes(gf) : 0;
+  DSRG_TRY(ws_reserve(ws, fixed + std::max(pass_mo, pass_f)));
+  int* flag = ws_take<int>(ws, 8);
+  DSRG_TRY(check_inputs_finite(prob, flag, st));
+  double* Wt = ws_take<double>(ws, (size_t)nv * nk);
+  double* U = ws_take<double>(ws, (size_t)nv * nk);
+  double* F = ws_take<double>(ws, nk2);
+  double* FV = ws_take<double>(ws, nk2);
+  double* Wsort = ws_take<double>(ws, nk2);
+  double* work = ws_take<double>(ws, 2 * nk2 + 8);
+  int* ib = ws_take<int>(ws, nk + 8);
+  double* Bf = ws_take<double>(ws, (size_t)rows * gf.np + 1);
+  double* epsf = ws_take<double>(ws, g.nh + nk + 1);
+  double* evals = ws_take<double>(ws, nk + 1);
+  const size_t base = ws.off;
+  double e_mo = 0.0;
+  if (e2_mo_in) e_mo = *e2_mo_in;
+  else DSRG_TRY(energy_pass(g, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, base, &e_mo, st));
+  double e_f = 0.0;
+  if (nk > 0) {
+    // F' = Vk^T diag(eps_v) Vk, recanonicalised: F' W = W eps'
+    const double* ev = prob->eps + g.nh;
+    DSRG_TRY(scale_rows(nv, nk, nv, ev, no, Wt, st));
+    DSRG_TRY(gemm_f64(nk, nk, nv, 1.0, no, nv, false, Wt, nk, false, 0.0, F, nk, 1, 0, 0, 0, st));
+    DSRG_TRY(eig_sym_jacobi(nk, F, FV, work, ib, 60, st));
+    DSRG_TRY(eig_sort(nk, F, FV, evals, Wsort, ib + 8, false, false, st));
+    // U = Vk W
+    DSRG_TRY(gemm_f64(nv, nk, nk, 1.0, no, nv, true, Wsort, nk, false, 0.0, U, nk, 1, 0, 0, 0, st));
+    // B' = [B_active | B_virtual U]
+    DSRG_TRY(copy_active(rows, g.na, g.np, gf.np, prob->B_hp, Bf, st));
+    DSRG_TRY(gemm_f64((int)rows, nk, nv, 1.0, prob->B_hp + g.na, g.np, true, U, nk, false, 0.0, Bf + g.na, gf.np,
+                      1, 0, 0, 0, st));
+    DSRG_CUDA(cudaMemcpyAsync(epsf, prob->eps, sizeof(double) * g.nh, cudaMemcpyDeviceToDevice, st));
+    DSRG_CUDA(cudaMemcpyAsync(epsf + g.nh, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
+    if (eps_fno_out)
+      DSRG_CUDA(cudaMemcpyAsync(eps_fno_out, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
+    DSRG_TRY(energy_pass(gf, Bf, epsf, prob->gamma1, prob->lambda2, ws, base, &e_f, st));
+  }
+  if (!isfinite(e_mo) || !isfinite(e_f)) return DSRG_FNO_ERR_NONFINITE;
+  *de_out = e_mo - e_f;
+  if (e2_fno_out) *e2_fno_out = e_f;
+  return DSRG_FNO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal launch API between the ABI layer and the kernels.
+#pragma once
+#include "common.cuh"
+
+namespace dsrg {
+
+// C[M][N] = alpha * op(A) op(B) + beta * C, float64, batched over blockIdx.z.
+//   a_kcontig: op(A)[m][k] = A[m*lda + k]   else A[k*lda + m]
+//   b_kcontig: op(B)[k][n] = B[n*ldb + k]   else B[k*ldb + n]
+int gemm_f64(int M, int N, int K, double alpha, const double* A, long lda, bool a_kcontig,
+             const double* B, long ldb, bool b_kcontig, double beta, double* C, long ldc,
+             int batch, long sa, long sb, long sc, cudaStream_t st);
+
+// Pair contraction nu^{ij}_{ab} = sum_Q B[Q][i][a] B[Q][j][b] for the listed
+// unordered hole pairs (i <= j), with the Eq. A7 epilogue:
+//   vv (a, b virtual): tau = nu R1(Delta), kappa = 2 nu - Delta tau -> tau/kap[slot][e][f]
+//   va / av (one active particle): t^{ij}_{ex} -> ts[i][j][e][x], t^{ji}_{ex}
+// ts may be null (energy-only passes).
+int pair_gemm_f64(const Geometry& g, const double* B, const double* eps, const int2* pairs,
+                  int npairs, double* tau, double* kap, double* ts, cudaStream_t st);
+
+// Dressed matrices of one batch (see dress.cu).
+struct DressDesc {
+  int kind;      // DressKind
+  int slot;      // first Tau slot of the group in the batch
+  int a, b;      // kind-specific indices (eigenvector column, core index, ...)
+  int out;       // output index in Sig
+};
+
+enum DressKind {
+  DRESS_CC_DIAG = 0,   // sigma = tau^{mm},                lambda = 2
+  DRESS_CC_SYM = 1,    // (tau + tau^T)/sqrt2,              lambda = 2
+  DRESS_CC_ANTI = 2,   // (tau - tau^T)/sqrt2,              lambda = 6
+  DRESS_CA_SYM = 3,    // sum_u W[u][k] (t^{mu} + t^{muT})/sqrt2, lambda = g_k
+  DRESS_CA_ANTI = 4,   // ... with minus,                   lambda = 3 g_k
+  DRESS_AA_SYM = 5,    // eigvec k of the symmetric aa block
+  DRESS_AA_ANTI = 6    // eigvec k of the antisymmetric aa block
+};
+
+struct DressAux {
+  const double* g1_evec;   // [na][na] (column k)
+  const double* g1_eval;   // [na]
+  const double* aas_evec;  // [ns][ns]  ns = na(na+1)/2
+  const double* aas_eval;
+  const double* aaa_evec;  // [nd][nd]  nd = na(na-1)/2
+  const double* aaa_eval;
+  const int* aa_slot;      // [na][na] -> slot offset of unordered pair (min,max) within aa group
+};
+
+// sigma_r from tau (and kappa): energy partials and Sig_r = sqrt|lambda_r| sigma_r[tau].
+int dress_f64(const Geometry& g, const DressDesc* d_desc, int ndesc, const DressAux& aux,
+              const double* tau, const double* kap, double* sig, double* sig_sign,
+              double* e_part, bool want_sig, cudaStream_t st);
+
+// D(upper tiles) += sum_r sign_r Sig_r Sig_r^T  (split-K partials, then reduction)
+int syrk_dressed_f64(int nv, int nr, const double* sig, const double* sig_sign, double* dpart,
+                     int nsplit, double* D, cudaStream_t st);
+
+// Symmetric-eigen helpers (eig.cu)
+int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
+                   cudaStream_t st);
+int eig_sort(int n, const double* A, const double* V, double* evals, double* evecs, int* rank,
+             bool descending, bool fix_sign, cudaStream_t st);
+
+// aa block of the hole 2-RDM in the swap-(anti)symmetric pair bases (dress.cu)
+int aa_blocks(int na, const double* g1, const double* lam2, double* Ms, double* Ma, cudaStream_t st);
+// out = (accumulate ? out : 0) + sum x, fixed summation order (dress.cu)
+int ordered_sum(const double* x, long n, double* out, bool accumulate, cudaStream_t st);
+
+// Singles and semi-internal terms (small_terms.cu)
+int t1_amplitudes(const Geometry& g, const double* ts, const double* eps, const double* f_hp,
+                  const double* g1, double* t1, cudaStream_t st);
+size_t small_terms_work_doubles(int nc, int na, int nv);
+int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1,
+                    const double* l2, double* D, double* work, cudaStream_t st);
+
+// Truncation and correction helpers (fno.cu)
+int truncate_ons(int nv, const double* ons, int mode, double thr, double ratio, int* nkept,
+                 cudaStream_t st);
+int symmetrize(int n, double* D, cudaStream_t st);
+int scale_rows(int nv, int ncol, long ld, const double* ev, const double* V, double* W,
+               cudaStream_t st);
+int copy_active(long rows, int na, int np, int npf, const double* B, double* Bf, cudaStream_t st);
+int check_finite(const double* x, long n, int* flag, cudaStream_t st);
+
+}  // namespace dsrg
