@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Throughput of the FNO SA-DSRG-PT2 hot path on GB300.
+
+One step = one whole solve of the workload: vv-class PT2 energy and D_vv
+(Eq. A12), natural orbitals (Eq. 8), and for every FNO cut the truncation
+(Eq. 10 with the near-degeneracy rule) and the discarded-virtual correction
+(Eq. 11, scalar part).  Inputs are seeded synthetic problems shaped like the
+paper's workloads; B is resident in HBM before the timed region and is larger
+than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched through torch.distributed.run) every rank solves its own
+copy of the workload (replicas: the path needs no exchange on one problem);
+value = solves of all ranks / max wall time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "sa_cas10_ncore60_nvir1200_naux3600"
+METRIC = "DSRG-PT2 D_vv+E2 solves/sec & GFLOP/s, fast vs FP64 GPU form at ≤1e-7 Eh"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--nslices", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the float64 GPU form (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="length of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def algorithmic_flops(p):
+    """F_V + F_D per solve: naux nvir^2 nh (nh+1) + nh^2 nvir^3."""
+    nh = p.ncore + p.nact
+    return float(p.naux) * p.nvir ** 2 * nh * (nh + 1) + float(nh) ** 2 * p.nvir ** 3
+
+
+def cuts_of(name):
+    from synth import CUTS
+    return CUTS.get(name, (98.5,))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_baseline(p, seconds):
+    """The oracle as it stands on the host cores: its vv-class energy and D_vv
+    term 4 for core-core pairs, one pair at a time until `seconds` pass; the
+    rate is scaled to a whole solve by the algorithmic flops covered."""
+    import numpy as np  # noqa: F401
+    import oracle as O
+    nc = p.ncore
+    pairs = [(m, n) for m in range(nc) for n in range(m, nc)]
+    t0 = time.perf_counter()
+    done = 0
+    covered = 0.0
+    for (m, n) in pairs:
+        O.e_vv(p, components=[[(m, n)] if m == n else [(m, n), (n, m)]])
+        O.dvv_terms(p, terms=(4,), core_pairs=[(m, n)])
+        done += 1
+        covered += 2.0 * p.naux * p.nvir ** 2 + (1 if m == n else 2) * float(p.nvir) ** 3
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    frac = covered / algorithmic_flops(p)
+    cores = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(i.get("num_threads", 1) for i in threadpool_info()) or cores
+    except Exception:
+        pass
+    return {"value": frac / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} core-core pair(s) of E_vv + D_vv term 4 in {dt:.1f} s, "
+                      f"{frac:.3e} of a solve's algorithmic flops, scaled"}
+
+
+def reference_arm(args):
+    from synth import workload
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload(args.workload)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(p, max(2.0, args.cpu_seconds / 4))
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(p, args.cpu_seconds))
+    v = sum(x["value"] for x in vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2312_07008_gb300 as pkg
+    from synth import workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = workload(args.workload)
+    cuts = cuts_of(args.workload)
+    nv = p.nvir
+    dev = torch.device("cuda", local)
+    gp = pkg.problem_from_synth(p, dev, pkg.SLICED_BF16, args.nslices)
+    d = torch.empty((nv, nv), dtype=torch.float64, device=dev)
+    on = torch.empty(nv, dtype=torch.float64, device=dev)
+    no = torch.empty((nv, nv), dtype=torch.float64, device=dev)
+
+    def step(prob):
+        e2 = pkg.dsrg_fno_vv_opdm(prob, d)
+        res = {"e2": e2}
+        for c in cuts:
+            k = pkg.dsrg_fno_truncate(nv, d, pkg.MODE_PO, c, 0.01, on, no)
+            de, ef = pkg.dsrg_fno_discarded_correction(prob, k, no, e2_mo=e2)
+            res[c] = (k, de)
+        return res
+
+    for _ in range(args.warmup):
+        step(gp)
+    stream = torch.cuda.current_stream()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    pkg.dsrg_fno_launch_count(reset=True)
+    pkg.dsrg_fno_profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        res = step(gp)
+    ev1.record(stream)
+    barrier()
+    pkg.dsrg_fno_profile_enable(False)
+    launches = pkg.dsrg_fno_launch_count()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.stop()
+    pair_ms, pair_n, pair_fl = pkg.dsrg_fno_profile_query("sliced_gemm_pair")
+    syrk_ms, syrk_n, syrk_fl = pkg.dsrg_fno_profile_query("sliced_gemm_syrk")
+    plain_ms, plain_n, plain_fl = pkg.dsrg_fno_profile_query("sliced_gemm_plain")
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    solves = args.steps * world
+    value = solves / (ms_max / 1e3)
+    flops = algorithmic_flops(p)
+
+    # ---- end to end through the C ABI, host buffers in pinned memory
+    host = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+            for k, v in (("B", p.B), ("eps", p.eps), ("g1", p.gamma1), ("l2", p.lambda2)) if v is not None}
+    dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    gp_e2e = pkg.Problem(p.ncore, p.nact, p.nvir, p.naux, dbuf["B"], dbuf["eps"], dbuf.get("g1"), dbuf.get("l2"),
+                         None, p.weights, p.s, pkg.SLICED_BF16, args.nslices)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    on_host = torch.empty(nv, dtype=torch.float64).pin_memory()
+    d2h = on_host.numel() * 8 + 8 * (1 + 2 * len(cuts))
+
+    def e2e_step():
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        r = step(gp_e2e)
+        on_host.copy_(on, non_blocking=True)
+        torch.cuda.synchronize()
+        return r
+
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = solves / (float(te.item()) / 1e3)
+
+    # ---- the plain float64 GPU form of the same solve
+    fp64 = None
+    if args.fp64_steps > 0:
+        gp64 = pkg.problem_from_synth(p, dev, pkg.FP64)
+        step(gp64)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp64_steps):
+            r64 = step(gp64)
+        f1.record(stream)
+        barrier()
+        fms = f0.elapsed_time(f1) / args.fp64_steps
+        fp64 = {"solves_per_s": 1e3 / fms, "s_per_solve": fms / 1e3, "gflops": flops / (fms / 1e3) / 1e9,
+                "fast_minus_fp64": {"e2": res["e2"] - r64["e2"],
+                                    **{f"de_{c}": res[c][1] - r64[c][1] for c in cuts},
+                                    **{f"nkept_{c}": [res[c][0], r64[c][0]] for c in cuts}}}
+
+    peaks, peak_kind = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    achieved = (pair_fl / (pair_ms / 1e3) / 1e12) if pair_ms > 0 else None
+    roofline = {"bound": "tensor", "kernel": "sliced_gemm_kernel (pair contraction, tcgen05 bf16 digit planes)",
+                "achieved": achieved, "peak": peak, "peak_kind": f"bf16 dense sustained, {peak_kind}",
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "launches": pair_n, "avg_launch_ms": pair_ms / max(pair_n, 1),
+                "executed_flops_per_launch": pair_fl / max(pair_n, 1),
+                "share_of_step": pair_ms / ms if ms > 0 else None,
+                "syrk": {"ms": syrk_ms, "launches": syrk_n,
+                         "tflops": (syrk_fl / (syrk_ms / 1e3) / 1e12) if syrk_ms > 0 else None},
+                "plain": {"ms": plain_ms, "launches": plain_n,
+                          "tflops": (plain_fl / (plain_ms / 1e3) / 1e12) if plain_ms > 0 else None}}
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": f"bf16 digit planes (k={args.nslices}) -> exact f32 level sums -> f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "ncore": p.ncore, "nact": p.nact, "nvir": p.nvir, "naux": p.naux,
+                   "nstates": len(p.weights), "s": p.s, "cuts_po": list(cuts), "nslices": args.nslices,
+                   "l2": f"inputs larger than L2 (B = {p.B.nbytes / 1e9:.2f} GB)", "parallelism": "replicas"},
+        "gflops": flops * value / 1e9,
+        "s_per_solve": ms_max / args.steps / 1e3,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "fp64_form": fp64,
+        "result": {"e2": res["e2"], **{f"nkept_{c}": res[c][0] for c in cuts}, **{f"de_{c}": res[c][1] for c in cuts}},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,30 @@
+/*
+ * dsrg_fno_debug.h - test hooks of libdsrg_fno.so (not part of the method).
+ *
+ * These entry points expose single building blocks of the fast form so that
+ * tests can check them in isolation.  They allocate their own device buffers
+ * (cudaMalloc/cudaFree), synchronise the device, and are not meant for
+ * production use.  Return values follow dsrg_fno_status.
+ */
+#ifndef DSRG_FNO_DEBUG_H
+#define DSRG_FNO_DEBUG_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* C[M][N] = A[M][K] B[N][K]^T with the exact bf16 digit-plane GEMM on the
+ * tensor cores (nslices planes, 3..5).  All arrays are host float64,
+ * row-major.  This is the contraction kernel of the fast form by itself. */
+int dsrg_fno_debug_sliced_gemm(int32_t nslices, int32_t M, int32_t N, int32_t K, const double* A,
+                               const double* B, double* C);
+
+/* Digit planes of rows[R][K] (host float64): planes[s][r][Kpad] as float
+ * values (host, R*Kpad*nslices) and the row exponents exps[R] (host). */
+int dsrg_fno_debug_slice_rows(int32_t nslices, int32_t R, int32_t K, const double* rows, float* planes,
+                              int32_t* exps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,32 @@
+/*
+ * dsrg_fno_profile.h - launch accounting of libdsrg_fno.so.
+ *
+ * While profiling is enabled, the library brackets every launch of its
+ * tensor-core contraction kernel and of its float64 pair-contraction kernel
+ * with CUDA events on the launching stream, and counts every kernel it
+ * launches.  Queries synchronise on the recorded events.  Not thread-safe
+ * with concurrent library calls on other threads.
+ */
+#ifndef DSRG_FNO_PROFILE_H
+#define DSRG_FNO_PROFILE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* enable != 0 starts recording (and clears earlier records); 0 stops. */
+void dsrg_fno_profile_enable(int32_t enable);
+
+/* Totals over the recorded launches of kernel `name` ("sliced_gemm_pair",
+ * "sliced_gemm_syrk", "sliced_gemm_plain", "pair_gemm_f64"): summed event
+ * time (ms), number of launches, and summed executed flops.  Returns 0. */
+int dsrg_fno_profile_query(const char* name, double* total_ms, int64_t* launches, double* flops);
+
+/* Number of kernels the library launched since the last reset; `reset`
+ * != 0 zeroes the counter after reading it. */
+int64_t dsrg_fno_launch_count(int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

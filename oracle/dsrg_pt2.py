@@ -249,8 +249,9 @@ def mp2_closed_shell(prob):
 # --------------------------------------------------------------------------
 # D_vv (Eq. A12, terms 1-12; the Lambda3 term 13 is omitted)
 # --------------------------------------------------------------------------
-def dvv_terms(prob, terms=range(1, 13), ts=None, t1=None):
-    """Returns {term number: [nvir][nvir] contribution} for Eq. A12."""
+def dvv_terms(prob, terms=range(1, 13), ts=None, t1=None, core_pairs=None):
+    """Returns {term number: [nvir][nvir] contribution} for Eq. A12.
+    `core_pairs` restricts term 4 to the listed unordered core pairs (m <= n)."""
     sp = spaces(prob)
     nc, na, nv = sp.nc, sp.na, sp.nv
     out = {}
@@ -280,12 +281,12 @@ def dvv_terms(prob, terms=range(1, 13), ts=None, t1=None):
                   + np.einsum("uvey,xf,uvxy->ef", taa, ta, L, optimize=True))
     if 4 in want:   # 2 t^{mn}_{ee'} tcheck^{mn}_{fe'}
         d = np.zeros((nv, nv))
-        for m in range(nc):
-            for n in range(m, nc):
-                T, _ = t2_vv(prob, m, n)          # t^{mn}; t^{nm} = T^T
-                d += 2.0 * T @ (2.0 * T - T.T).T
-                if n != m:
-                    d += 2.0 * T.T @ (2.0 * T.T - T).T
+        plist = core_pairs if core_pairs is not None else [(m, n) for m in range(nc) for n in range(m, nc)]
+        for m, n in plist:
+            T, _ = t2_vv(prob, m, n)          # t^{mn}; t^{nm} = T^T
+            d += 2.0 * T @ (2.0 * T - T.T).T
+            if n != m:
+                d += 2.0 * T.T @ (2.0 * T.T - T).T
         out[4] = d
     if na and 5 in want:   # S(t^{mu}_{ee'} tcheck^{mv}_{fe'}) Gamma^u_v
         d = np.zeros((nv, nv))

@@ -22,6 +22,11 @@ EXPORTED = (
     "dsrg_fno_discarded_correction",
     "dsrg_fno_status_string",
     "dsrg_fno_release",
+    "dsrg_fno_debug_sliced_gemm",
+    "dsrg_fno_debug_slice_rows",
+    "dsrg_fno_profile_enable",
+    "dsrg_fno_profile_query",
+    "dsrg_fno_launch_count",
 )
 
 FP64 = 0
@@ -66,6 +71,16 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_status_string.argtypes = [ctypes.c_int]
     lib.dsrg_fno_status_string.restype = ctypes.c_char_p
     lib.dsrg_fno_release.argtypes = []
+    dp = ctypes.POINTER(d)
+    lib.dsrg_fno_debug_sliced_gemm.argtypes = [i32, i32, i32, i32, dp, dp, dp]
+    lib.dsrg_fno_debug_slice_rows.argtypes = [i32, i32, i32, dp, ctypes.POINTER(ctypes.c_float),
+                                              ctypes.POINTER(i32)]
+    lib.dsrg_fno_profile_enable.argtypes = [i32]
+    lib.dsrg_fno_profile_enable.restype = None
+    lib.dsrg_fno_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(d)]
+    lib.dsrg_fno_launch_count.argtypes = [i32]
+    lib.dsrg_fno_launch_count.restype = ctypes.c_int64
     for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_truncate", "dsrg_fno_discarded_correction"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
@@ -146,3 +161,19 @@ def dsrg_fno_discarded_correction(prob: Problem, nkept, no, e2_mo=None, eps_fno_
 
 def dsrg_fno_release():
     load().dsrg_fno_release()
+
+
+def dsrg_fno_profile_enable(enable: bool):
+    load().dsrg_fno_profile_enable(1 if enable else 0)
+
+
+def dsrg_fno_profile_query(name: str):
+    """(total ms, launches, executed flops) of the recorded launches of `name`."""
+    t, f = ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int64()
+    load().dsrg_fno_profile_query(name.encode(), ctypes.byref(t), ctypes.byref(n), ctypes.byref(f))
+    return t.value, n.value, f.value
+
+
+def dsrg_fno_launch_count(reset: bool = False) -> int:
+    return load().dsrg_fno_launch_count(1 if reset else 0)

@@ -135,7 +135,8 @@ static int validate(const dsrg_fno_problem* p) {
   if (p->ncore + p->nact == 0 || p->nvir == 0) return DSRG_FNO_ERR_ARG;
   if (!(p->s >= 0.0) || !isfinite(p->s)) return DSRG_FNO_ERR_ARG;
   if (p->precision != DSRG_FNO_FP64 && p->precision != DSRG_FNO_SLICED_BF16) return DSRG_FNO_ERR_ARG;
-  if (p->precision == DSRG_FNO_SLICED_BF16) return DSRG_FNO_ERR_UNSUPPORTED;
+  if (p->precision == DSRG_FNO_SLICED_BF16 && p->nslices != 0 && (p->nslices < 3 || p->nslices > 5))
+    return DSRG_FNO_ERR_UNSUPPORTED;
   if (p->naux > 0 && !is_device_ptr(p->B_hp)) return DSRG_FNO_ERR_ARG;
   if (!is_device_ptr(p->eps)) return DSRG_FNO_ERR_ARG;
   if (p->nact > 0 && (!is_device_ptr(p->gamma1) || !is_device_ptr(p->lambda2))) return DSRG_FNO_ERR_ARG;
@@ -178,12 +179,27 @@ struct PassBuffers {
   double *g1A, *g1V, *g1W, *MsA, *MsV, *MsW, *MaA, *MaV, *MaW;
   int* status;
   int nsplit;
+  // fast form
+  int ks;             // digit planes (0 = float64 form)
+  int kpad_q, kpad_v; // padded contraction lengths (naux, nvir)
+  __nv_bfloat16 *planes_b, *planes_s;
+  int *exps_b, *exps_s, *err;
+  double* nu;
 };
+
+static const int DEFAULT_SLICES = 5;
+
+static int slices_of(const dsrg_fno_problem* p) {
+  if (p->precision != DSRG_FNO_SLICED_BF16) return 0;
+  return p->nslices ? p->nslices : DEFAULT_SLICES;
+}
 
 static size_t doubles(size_t n) { return ws_bytes(n, sizeof(double)); }
 
-static long pair_cap_for_budget(int nv, size_t budget) {
-  const double per_pair = 4.0 * (double)nv * nv * 8.0 + 1024.0;
+static long pair_cap_for_budget(int nv, int np, int ks, size_t budget) {
+  // tau + kappa + two dressed matrices per pair (+ nu and the dressed planes in the fast form)
+  double per_pair = 4.0 * (double)nv * nv * 8.0 + 1024.0;
+  if (ks) per_pair += (double)np * np * 8.0 + 2.0 * ks * 2.0 * (double)nv * (nv + 64);
   long cap = (long)(budget / per_pair);
   return std::max<long>(cap, 1);
 }
@@ -218,14 +234,34 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
     aux.aaa_eval = W.MaA;
   }
   const int ntd = ceil_div(g.nv, 32);
+  if (W.ks) {
+    // digit planes of B: rows (hole, particle), contraction over Q
+    const long rows = (long)g.nh * g.np;
+    DSRG_TRY(slice_rows(W.ks, B, rows, g.nq, 1, rows, W.kpad_q, W.planes_b, W.exps_b, st));
+  }
   for (size_t bi = 0; bi < P.batches.size(); ++bi) {
     const Batch& b = P.batches[bi];
-    DSRG_TRY(pair_gemm_f64(g, B, eps, W.pairs + b.pair_begin, b.npairs, W.tau, W.kap, want_d ? W.ts : nullptr,
-                           st));
+    double* ts = want_d ? W.ts : nullptr;
+    if (W.ks) {
+      DSRG_TRY(sliced_pair_gemm(W.ks, g, W.planes_b, W.exps_b, W.kpad_q, W.pairs + b.pair_begin, b.npairs,
+                                ts == nullptr, W.nu, W.err, st));
+      DSRG_TRY(pair_epilogue(g, eps, W.pairs + b.pair_begin, b.npairs, W.nu, W.tau, W.kap, ts, st));
+    } else {
+      DSRG_TRY(pair_gemm_f64(g, B, eps, W.pairs + b.pair_begin, b.npairs, W.tau, W.kap, ts, st));
+    }
     DSRG_TRY(dress_f64(g, W.desc + b.desc_begin, b.ndesc, aux, W.tau, W.kap, W.sig, W.sig_sign, W.e_part, want_d,
                        st));
     DSRG_TRY(ordered_sum(W.e_part, (long)b.ndesc * ntd * ntd, W.e_acc, bi > 0, st));
-    if (want_d) DSRG_TRY(syrk_dressed_f64(g.nv, b.ndesc, W.sig, W.sig_sign, W.dpart, W.nsplit, D, st));
+    if (want_d) {
+      if (W.ks) {
+        const long rows = (long)b.ndesc * g.nv;
+        DSRG_TRY(slice_rows(W.ks, W.sig, rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, st));
+        DSRG_TRY(sliced_syrk(W.ks, g.nv, b.ndesc, W.planes_s, W.exps_s, W.kpad_v, W.sig_sign, W.dpart, W.nsplit, D,
+                             W.err, st));
+      } else {
+        DSRG_TRY(syrk_dressed_f64(g.nv, b.ndesc, W.sig, W.sig_sign, W.dpart, W.nsplit, D, st));
+      }
+    }
   }
   if (P.batches.empty()) DSRG_CUDA(cudaMemsetAsync(W.e_acc, 0, sizeof(double), st));
   return DSRG_FNO_OK;
@@ -240,7 +276,7 @@ static int nsplit_for(int nv, int ndesc) {
 }
 
 // Carves the pass buffers out of the workspace (sizes must match pass_bytes).
-static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nsplit) {
+static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nsplit, int ks) {
   const size_t nv2 = (size_t)g.nv * g.nv;
   const int na = g.na, ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
   const int ntd = ceil_div(g.nv, 32);
@@ -258,11 +294,19 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
   b += 2 * doubles((size_t)ns * ns + 1) + doubles(2 * (size_t)ns * ns + 8);
   b += 2 * doubles((size_t)nd * nd + 1) + doubles(2 * (size_t)nd * nd + 8);
   b += ws_bytes(8, sizeof(int));
+  if (ks) {
+    const size_t rows = (size_t)g.nh * g.np;
+    b += ws_bytes((size_t)ks * rows * pad64(g.nq), 2) + ws_bytes(rows, sizeof(int));
+    b += doubles((size_t)P.max_pairs * g.np * g.np);
+    if (want_d)
+      b += ws_bytes((size_t)ks * P.max_desc * g.nv * pad64(g.nv), 2) + ws_bytes((size_t)P.max_desc * g.nv, sizeof(int));
+    b += ws_bytes(8, sizeof(int));
+  }
   return b;
 }
 
-static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want_d, int nsplit, PassBuffers& W,
-                      cudaStream_t st) {
+static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want_d, int nsplit, int ks,
+                      PassBuffers& W, cudaStream_t st) {
   const size_t nv2 = (size_t)g.nv * g.nv;
   const int na = g.na, ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
   const int ntd = ceil_div(g.nv, 32);
@@ -289,6 +333,22 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
   W.status = ws_take<int>(ws, 8);
   W.nsplit = nsplit;
   if (!W.status) return DSRG_FNO_ERR_NOMEM;
+  W.ks = ks;
+  if (ks) {
+    const size_t rows = (size_t)g.nh * g.np;
+    W.kpad_q = pad64(g.nq);
+    W.kpad_v = pad64(g.nv);
+    W.planes_b = ws_take<__nv_bfloat16>(ws, (size_t)ks * rows * W.kpad_q);
+    W.exps_b = ws_take<int>(ws, rows);
+    W.nu = ws_take<double>(ws, (size_t)P.max_pairs * g.np * g.np);
+    if (want_d) {
+      W.planes_s = ws_take<__nv_bfloat16>(ws, (size_t)ks * P.max_desc * g.nv * W.kpad_v);
+      W.exps_s = ws_take<int>(ws, (size_t)P.max_desc * g.nv);
+    }
+    W.err = ws_take<int>(ws, 8);
+    if (!W.err) return DSRG_FNO_ERR_NOMEM;
+    DSRG_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), st));
+  }
   if (!P.pairs.empty())
     DSRG_CUDA(cudaMemcpyAsync(W.pairs, P.pairs.data(), P.pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   if (!P.desc.empty())
@@ -309,26 +369,35 @@ static Geometry geometry_of(const dsrg_fno_problem* p) {
   return g;
 }
 
+static int read_error_flag(const int* err, cudaStream_t st) {
+  if (!err) return DSRG_FNO_OK;
+  int h = 0;
+  DSRG_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  return h ? DSRG_FNO_ERR_TIMEOUT : DSRG_FNO_OK;
+}
+
 // Energy-only pass for an arbitrary geometry (used for the MO and FNO bases).
-static int energy_pass(const Geometry& g, const double* B, const double* eps, const double* gamma1,
-                       const double* lambda2, Workspace& ws, size_t base_off, double* e_out, cudaStream_t st) {
+static int energy_pass(const Geometry& g, int ks, const double* B, const double* eps, const double* gamma1,
+                       const double* lambda2, Workspace& ws, size_t base_off, size_t budget, double* e_out,
+                       cudaStream_t st) {
   Plan P;
-  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, device_budget()), P);
+  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, budget), P);
   ws.off = base_off;
   PassBuffers W{};
-  size_t need = base_off + pass_bytes(g, P, false, 1);
+  size_t need = base_off + pass_bytes(g, P, false, 1, ks);
   if (need > ws.cap) return DSRG_FNO_ERR_NOMEM;
-  DSRG_TRY(carve_pass(ws, g, P, false, 1, W, st));
+  DSRG_TRY(carve_pass(ws, g, P, false, 1, ks, W, st));
   DSRG_TRY(run_pass(g, B, eps, gamma1, lambda2, P, W, false, nullptr, st));
   DSRG_CUDA(cudaMemcpyAsync(e_out, W.e_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
   DSRG_CUDA(cudaStreamSynchronize(st));
-  return DSRG_FNO_OK;
+  return read_error_flag(W.err, st);
 }
 
-static size_t energy_pass_bytes(const Geometry& g) {
+static size_t energy_pass_bytes(const Geometry& g, int ks, size_t budget) {
   Plan P;
-  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, device_budget()), P);
-  return pass_bytes(g, P, false, 1);
+  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, budget), P);
+  return pass_bytes(g, P, false, 1, ks);
 }
 
 }  // namespace dsrg
@@ -376,10 +445,12 @@ int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stre
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
   const Geometry g = geometry_of(prob);
-  DSRG_TRY(ws_reserve(ws, energy_pass_bytes(g) + ws_bytes(8, sizeof(int))));
+  const int ks = slices_of(prob);
+  const size_t budget = device_budget() + ws.cap / 2;
+  DSRG_TRY(ws_reserve(ws, energy_pass_bytes(g, ks, budget) + ws_bytes(8, sizeof(int))));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
-  return energy_pass(g, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, ws.off, e2_out, st);
+  return energy_pass(g, ks, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, ws.off, budget, e2_out, st);
 }
 
 int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out, void* stream) {
@@ -390,17 +461,18 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
   const Geometry g = geometry_of(prob);
+  const int ks = slices_of(prob);
   Plan P;
-  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, device_budget()), P);
+  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, device_budget() + ws.cap / 2), P);
   const int nsplit = nsplit_for(g.nv, P.max_desc);
   const size_t small = small_terms_work_doubles(g.nc, g.na, g.nv);
-  size_t need = ws_bytes(8, sizeof(int)) + pass_bytes(g, P, true, nsplit) + doubles((size_t)g.nh * g.nv) +
+  size_t need = ws_bytes(8, sizeof(int)) + pass_bytes(g, P, true, nsplit, ks) + doubles((size_t)g.nh * g.nv) +
                 doubles(small + 1);
   DSRG_TRY(ws_reserve(ws, need));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
   PassBuffers W{};
-  DSRG_TRY(carve_pass(ws, g, P, true, nsplit, W, st));
+  DSRG_TRY(carve_pass(ws, g, P, true, nsplit, ks, W, st));
   double* t1 = ws_take<double>(ws, (size_t)g.nh * g.nv);
   double* work = ws_take<double>(ws, small + 1);
   const size_t nv2 = (size_t)g.nv * g.nv;
@@ -418,6 +490,7 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   DSRG_CUDA(cudaMemcpyAsync(&e, W.e_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
   DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   DSRG_CUDA(cudaStreamSynchronize(st));
+  DSRG_TRY(read_error_flag(W.err, st));
   if (h || !isfinite(e)) return DSRG_FNO_ERR_NONFINITE;
   if (e2_out) *e2_out = e;
   return DSRG_FNO_OK;
@@ -472,9 +545,16 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
   size_t fixed = ws_bytes(8, sizeof(int)) + doubles((size_t)nv * nk) * 2 + doubles(nk2) * 3 + doubles(2 * nk2 + 8) +
                  ws_bytes(nk + 8, sizeof(int)) + doubles((size_t)rows * gf.np + 1) + doubles(g.nh + nk + 1) +
                  doubles(nk + 1);
-  size_t pass_mo = e2_mo_in ? 0 : energy_pass_bytes(g);
-  size_t pass_f = nk > 0 ? energy_pass_bytes(gf) : 0;
-  DSRG_TRY(ws_reserve(ws, fixed + std::max(pass_mo, pass_f)));
+  const int ks = slices_of(prob);
+  const size_t budget = device_budget() + ws.cap / 2;
+  size_t pass_mo = e2_mo_in ? 0 : energy_pass_bytes(g, ks, budget);
+  size_t pass_f = nk > 0 ? energy_pass_bytes(gf, ks, budget) : 0;
+  const int kpv = pad64(nv);
+  size_t xform = 0;
+  if (ks && nk > 0)
+    xform = ws_bytes((size_t)ks * rows * kpv, 2) + ws_bytes(rows, sizeof(int)) + ws_bytes((size_t)ks * nk * kpv, 2) +
+            ws_bytes(nk, sizeof(int)) + ws_bytes(8, sizeof(int));
+  DSRG_TRY(ws_reserve(ws, fixed + std::max(std::max(pass_mo, pass_f), xform)));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
   double* Wt = ws_take<double>(ws, (size_t)nv * nk);
@@ -490,7 +570,8 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
   const size_t base = ws.off;
   double e_mo = 0.0;
   if (e2_mo_in) e_mo = *e2_mo_in;
-  else DSRG_TRY(energy_pass(g, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, base, &e_mo, st));
+  else
+    DSRG_TRY(energy_pass(g, ks, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, base, budget, &e_mo, st));
   double e_f = 0.0;
   if (nk > 0) {
     // F' = Vk^T diag(eps_v) Vk, recanonicalised: F' W = W eps'
@@ -503,13 +584,29 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
     DSRG_TRY(gemm_f64(nv, nk, nk, 1.0, no, nv, true, Wsort, nk, false, 0.0, U, nk, 1, 0, 0, 0, st));
     // B' = [B_active | B_virtual U]
     DSRG_TRY(copy_active(rows, g.na, g.np, gf.np, prob->B_hp, Bf, st));
-    DSRG_TRY(gemm_f64((int)rows, nk, nv, 1.0, prob->B_hp + g.na, g.np, true, U, nk, false, 0.0, Bf + g.na, gf.np,
-                      1, 0, 0, 0, st));
+    if (ks) {
+      ws.off = base;
+      __nv_bfloat16* pa = ws_take<__nv_bfloat16>(ws, (size_t)ks * rows * kpv);
+      int* ea = ws_take<int>(ws, rows);
+      __nv_bfloat16* pb = ws_take<__nv_bfloat16>(ws, (size_t)ks * nk * kpv);
+      int* eb = ws_take<int>(ws, nk);
+      int* err = ws_take<int>(ws, 8);
+      if (!err) return DSRG_FNO_ERR_NOMEM;
+      DSRG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+      // rows (Q, h) over the virtual index e, and U^T rows l over e
+      DSRG_TRY(slice_rows(ks, prob->B_hp + g.na, rows, nv, g.np, 1, kpv, pa, ea, st));
+      DSRG_TRY(slice_rows(ks, U, nk, nv, 1, nk, kpv, pb, eb, st));
+      DSRG_TRY(sliced_plain_gemm(ks, (int)rows, nk, pa, ea, pb, eb, kpv, Bf + g.na, gf.np, err, st));
+      DSRG_TRY(read_error_flag(err, st));
+    } else {
+      DSRG_TRY(gemm_f64((int)rows, nk, nv, 1.0, prob->B_hp + g.na, g.np, true, U, nk, false, 0.0, Bf + g.na, gf.np,
+                        1, 0, 0, 0, st));
+    }
     DSRG_CUDA(cudaMemcpyAsync(epsf, prob->eps, sizeof(double) * g.nh, cudaMemcpyDeviceToDevice, st));
     DSRG_CUDA(cudaMemcpyAsync(epsf + g.nh, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
     if (eps_fno_out)
       DSRG_CUDA(cudaMemcpyAsync(eps_fno_out, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
-    DSRG_TRY(energy_pass(gf, Bf, epsf, prob->gamma1, prob->lambda2, ws, base, &e_f, st));
+    DSRG_TRY(energy_pass(gf, ks, Bf, epsf, prob->gamma1, prob->lambda2, ws, base, budget, &e_f, st));
   }
   if (!isfinite(e_mo) || !isfinite(e_f)) return DSRG_FNO_ERR_NONFINITE;
   *de_out = e_mo - e_f;

@@ -29,7 +29,17 @@ namespace dsrg {
     if (s_ != DSRG_FNO_OK) return s_;                                         \
   } while (0)
 
-#define DSRG_LAUNCH_CHECK() DSRG_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by this check, which also
+// feeds the launch counter of the profiling interface.
+void count_launch();
+bool profiling();
+void prof_begin(const char* name, double flops, cudaStream_t st, void** token);
+void prof_end(void* token, cudaStream_t st);
+#define DSRG_LAUNCH_CHECK() \
+  do {                      \
+    count_launch();         \
+    DSRG_CUDA(cudaGetLastError()); \
+  } while (0)
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 

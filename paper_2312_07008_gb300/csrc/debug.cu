@@ -1,0 +1,64 @@
+// Test hooks of the fast form (include/dsrg_fno_debug.h).
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "../../include/dsrg_fno_debug.h"
+#include "kernels.h"
+
+using namespace dsrg;
+
+namespace {
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+extern "C" int dsrg_fno_debug_sliced_gemm(int32_t ks, int32_t M, int32_t N, int32_t K, const double* A,
+                                          const double* B, double* C) {
+  if (ks < 3 || ks > 5 || M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return DSRG_FNO_ERR_ARG;
+  const int kp = pad64(K);
+  DevBuf dA, dB, dC, pa, pb, ea, eb, err;
+  DSRG_CUDA(cudaMalloc(&dA.p, sizeof(double) * M * K));
+  DSRG_CUDA(cudaMalloc(&dB.p, sizeof(double) * N * K));
+  DSRG_CUDA(cudaMalloc(&dC.p, sizeof(double) * M * N));
+  DSRG_CUDA(cudaMalloc(&pa.p, 2L * ks * M * kp));
+  DSRG_CUDA(cudaMalloc(&pb.p, 2L * ks * N * kp));
+  DSRG_CUDA(cudaMalloc(&ea.p, sizeof(int) * M));
+  DSRG_CUDA(cudaMalloc(&eb.p, sizeof(int) * N));
+  DSRG_CUDA(cudaMalloc(&err.p, sizeof(int)));
+  DSRG_CUDA(cudaMemset(err.p, 0, sizeof(int)));
+  DSRG_CUDA(cudaMemcpy(dA.p, A, sizeof(double) * M * K, cudaMemcpyHostToDevice));
+  DSRG_CUDA(cudaMemcpy(dB.p, B, sizeof(double) * N * K, cudaMemcpyHostToDevice));
+  cudaStream_t st = 0;
+  DSRG_TRY(slice_rows(ks, (double*)dA.p, M, K, K, 1, kp, (__nv_bfloat16*)pa.p, (int*)ea.p, st));
+  DSRG_TRY(slice_rows(ks, (double*)dB.p, N, K, K, 1, kp, (__nv_bfloat16*)pb.p, (int*)eb.p, st));
+  DSRG_TRY(sliced_plain_gemm(ks, M, N, (__nv_bfloat16*)pa.p, (int*)ea.p, (__nv_bfloat16*)pb.p, (int*)eb.p, kp,
+                             (double*)dC.p, N, (int*)err.p, st));
+  DSRG_CUDA(cudaDeviceSynchronize());
+  int h = 0;
+  DSRG_CUDA(cudaMemcpy(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  DSRG_CUDA(cudaMemcpy(C, dC.p, sizeof(double) * M * N, cudaMemcpyDeviceToHost));
+  return h ? DSRG_FNO_ERR_TIMEOUT : DSRG_FNO_OK;
+}
+
+extern "C" int dsrg_fno_debug_slice_rows(int32_t ks, int32_t R, int32_t K, const double* rows, float* planes,
+                                         int32_t* exps) {
+  if (ks < 3 || ks > 5 || R <= 0 || K <= 0 || !rows || !planes || !exps) return DSRG_FNO_ERR_ARG;
+  const int kp = pad64(K);
+  DevBuf d, p, e;
+  DSRG_CUDA(cudaMalloc(&d.p, sizeof(double) * R * K));
+  DSRG_CUDA(cudaMalloc(&p.p, 2L * ks * R * kp));
+  DSRG_CUDA(cudaMalloc(&e.p, sizeof(int) * R));
+  DSRG_CUDA(cudaMemcpy(d.p, rows, sizeof(double) * R * K, cudaMemcpyHostToDevice));
+  DSRG_TRY(slice_rows(ks, (double*)d.p, R, K, K, 1, kp, (__nv_bfloat16*)p.p, (int*)e.p, 0));
+  DSRG_CUDA(cudaDeviceSynchronize());
+  std::vector<__nv_bfloat16> h((size_t)ks * R * kp);
+  DSRG_CUDA(cudaMemcpy(h.data(), p.p, h.size() * 2, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < h.size(); ++i) planes[i] = __bfloat162float(h[i]);
+  DSRG_CUDA(cudaMemcpy(exps, e.p, sizeof(int) * R, cudaMemcpyDeviceToHost));
+  return DSRG_FNO_OK;
+}

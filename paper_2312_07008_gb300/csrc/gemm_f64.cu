@@ -263,8 +263,11 @@ int pair_gemm_f64(const Geometry& g, const double* B, const double* eps, const i
                   double* tau, double* kap, double* ts, cudaStream_t st) {
   if (npairs <= 0) return DSRG_FNO_OK;
   dim3 grid(ceil_div(g.np, TN), ceil_div(g.np, TM), npairs);
+  void* tok = nullptr;
+  if (profiling()) prof_begin("pair_gemm_f64", 2.0 * g.np * (double)g.np * g.nq * npairs, st, &tok);
   pair_gemm_f64_kernel<<<grid, NT, 0, st>>>(g, B, eps, pairs, tau, kap, ts);
   DSRG_LAUNCH_CHECK();
+  prof_end(tok, st);
   return DSRG_FNO_OK;
 }
 

@@ -1,5 +1,7 @@
 // Internal launch API between the ABI layer and the kernels.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace dsrg {
@@ -73,6 +75,19 @@ int t1_amplitudes(const Geometry& g, const double* ts, const double* eps, const 
 size_t small_terms_work_doubles(int nc, int na, int nv);
 int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1,
                     const double* l2, double* D, double* work, cudaStream_t st);
+
+// Fast form: exact bf16 digit planes on tcgen05 (sliced.cu)
+int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
+               int* exps, cudaStream_t st);
+int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
+                     const int2* pairs, int npairs, bool energy_only, double* nu, int* err, cudaStream_t st);
+int pair_epilogue(const Geometry& g, const double* eps, const int2* pairs, int npairs, const double* nu,
+                  double* tau, double* kap, double* ts, cudaStream_t st);
+int sliced_syrk(int KS, int nv, int nr, const __nv_bfloat16* planes, const int* exps, int Kpad,
+                const double* sign, double* dpart, int nsplit, double* D, int* err, cudaStream_t st);
+int sliced_plain_gemm(int KS, int M, int N, const __nv_bfloat16* pa, const int* ea, const __nv_bfloat16* pb,
+                      const int* eb, int Kpad, double* C, long ldc, int* err, cudaStream_t st);
+inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
 // Truncation and correction helpers (fno.cu)
 int truncate_ons(int nv, const double* ons, int mode, double thr, double ratio, int* nkept,

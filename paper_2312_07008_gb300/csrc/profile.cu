@@ -1,0 +1,88 @@
+// Launch accounting (include/dsrg_fno_profile.h).
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/dsrg_fno_profile.h"
+#include "kernels.h"
+
+namespace dsrg {
+
+static std::atomic<long long> g_launches{0};
+static bool g_prof = false;
+
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a, b;
+  double flops;
+};
+static std::vector<ProfRec> g_recs;
+static std::mutex g_prof_mutex;
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool profiling() { return g_prof; }
+
+void prof_begin(const char* name, double flops, cudaStream_t st, void** token) {
+  *token = nullptr;
+  if (!g_prof) return;
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  ProfRec r;
+  r.name = name;
+  r.flops = flops;
+  cudaEventCreate(&r.a);
+  cudaEventCreate(&r.b);
+  cudaEventRecord(r.a, st);
+  g_recs.push_back(r);
+  *token = reinterpret_cast<void*>(g_recs.size());
+}
+
+void prof_end(void* token, cudaStream_t st) {
+  if (!token) return;
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  size_t i = reinterpret_cast<size_t>(token) - 1;
+  if (i < g_recs.size()) cudaEventRecord(g_recs[i].b, st);
+}
+
+}  // namespace dsrg
+
+using namespace dsrg;
+
+extern "C" void dsrg_fno_profile_enable(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  if (enable) {
+    for (auto& r : g_recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    g_recs.clear();
+  }
+  g_prof = enable != 0;
+}
+
+extern "C" int dsrg_fno_profile_query(const char* name, double* total_ms, int64_t* launches, double* flops) {
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  double t = 0.0, f = 0.0;
+  int64_t n = 0;
+  for (auto& r : g_recs) {
+    if (name && r.name != name) continue;
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      t += ms;
+      f += r.flops;
+      ++n;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = n;
+  if (flops) *flops = f;
+  return DSRG_FNO_OK;
+}
+
+extern "C" int64_t dsrg_fno_launch_count(int32_t reset) {
+  long long v = reset ? g_launches.exchange(0) : g_launches.load();
+  return (int64_t)v;
+}

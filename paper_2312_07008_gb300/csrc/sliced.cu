@@ -1,0 +1,716 @@
+// Fast form of the contractions: exact bfloat16 digit planes on the tcgen05
+// tensor cores.
+//
+// Staging.  Each float64 row v[k] (k = contraction index) gets a power-of-two
+// scale 2^e_row with max_k |v| < 2^e_row, and the scaled value x = v 2^-e_row
+// is rounded to X = round(x 2^F), F = 6 + 7 (KS - 1), then written in balanced
+// radix 128:  X = sum_s d_s 128^(KS-1-s),  d_s integer in [-64, 64], exact in
+// bfloat16.  Hence x = 2^-6 sum_s d_s 2^-7s up to 2^-(F+1).
+//
+// Products.  For two rows a, b:  x_a . x_b = 2^-12 sum_L 2^-7L S_L with the
+// level sums S_L = sum_{s+t=L} sum_k d_s(a,k) d_t(b,k).  Only levels
+// L <= KS-1 are formed (triangular truncation, KS(KS+1)/2 digit products).
+// Every digit product is an integer of magnitude <= 2^12, so a level sum over
+// a chunk of 512 k-values holds at most (L+1) 2^21 <= 2^24 in magnitude and
+// the float32 accumulator of the tensor core represents it exactly.
+//
+// Kernel.  Persistent, warp-specialised: warp 0 issues TMA loads of all KS
+// planes of a 64-wide k block (128-byte swizzle) into a 2-3 stage ring, warp 1
+// issues tcgen05.mma into per-level TMEM accumulators (two sets, double
+// buffered), warps 2-5 drain each finished chunk with tcgen05.ld and add
+// 2^-7L S_L into a float32-pair (double-float) accumulator per element.  At the
+// end of a tile the float64 result is written out.  Every mbarrier wait is
+// bounded; on expiry the kernel records the failure and leaves.
+#include <cuda.h>
+
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace dsrg {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BKE = 64;            // k elements per block (128 bytes of bf16)
+constexpr int KCHUNK_BLOCKS = 8;   // 512 k-values per exact level sum
+constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
+
+enum { MODE_PAIR = 0, MODE_SYRK = 1, MODE_PLAIN = 2 };
+
+// ---------------------------------------------------------------- staging
+// Row exponent e with max |v| < 2^e (frexp exponent of the row maximum).
+__device__ __forceinline__ int row_exponent(double maxabs) {
+  long long b = __double_as_longlong(maxabs);
+  int E = (int)((b >> 52) & 0x7FF);
+  return E == 0 ? -1022 : E - 1022;
+}
+
+template <int KS>
+__device__ __forceinline__ void digits_of(double v, int e_row, int* d) {
+  constexpr int F = 6 + 7 * (KS - 1);
+  long long b = __double_as_longlong(v);
+  int E = (int)((b >> 52) & 0x7FF);
+  long long X = 0;
+  if (E != 0) {
+    long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    int sh = 1075 - E - F + e_row;  // >= 5 for KS <= 7 because |v| < 2^e_row
+    if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
+    if (b < 0) X = -X;
+  }
+#pragma unroll
+  for (int s = KS - 1; s >= 1; --s) {
+    long long r = ((X + 64) & 127) - 64;
+    d[s] = (int)r;
+    X = (X - r) >> 7;
+  }
+  d[0] = (int)X;
+}
+
+// planes[s][row][k] (bf16, k padded to Kpad with zeros), exps[row].
+// Source element (row, k) at src[row * rs + k * ks]; one of rs, ks is 1.
+template <int KS>
+__global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ src, long R, int K, long rs,
+                                                         long ks, int Kpad, __nv_bfloat16* __restrict__ planes,
+                                                         int* __restrict__ exps) {
+  __shared__ double tile[32][33];
+  __shared__ int s_exp[32];
+  const long row0 = (long)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const bool kfast = (ks == 1);
+  const int myrow = threadIdx.x >> 3, part = threadIdx.x & 7;  // 32 rows x 8 parts
+  double mx = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 32) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int r = kfast ? ty + 8 * i : tx;
+      int k = kfast ? tx : ty + 8 * i;
+      long row = row0 + r;
+      double v = 0.0;
+      if (row < R && k0 + k < K) v = src[row * rs + (long)(k0 + k) * ks];
+      tile[r][k] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mx = fmax(mx, fabs(tile[myrow][part * 4 + j]));
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (part == 0) {
+    int e = row_exponent(mx);
+    s_exp[myrow] = e;
+    if (row0 + myrow < R) exps[row0 + myrow] = e;
+  }
+  __syncthreads();
+  const int e_row = s_exp[myrow];
+  const long row = row0 + myrow;
+  for (int k0 = 0; k0 < Kpad; k0 += 32) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int r = kfast ? ty + 8 * i : tx;
+      int k = kfast ? tx : ty + 8 * i;
+      long rr = row0 + r;
+      double v = 0.0;
+      if (rr < R && k0 + k < K) v = src[rr * rs + (long)(k0 + k) * ks];
+      tile[r][k] = v;
+    }
+    __syncthreads();
+    if (row < R) {
+      int dg[4][KS];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) digits_of<KS>(tile[myrow][part * 4 + j], e_row, dg[j]);
+#pragma unroll
+      for (int s = 0; s < KS; ++s) {
+        __nv_bfloat16 h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) h[j] = __float2bfloat16_rn((float)dg[j][s]);
+        uint2 pk;
+        pk.x = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+        pk.y = (uint32_t)__bfloat16_as_ushort(h[2]) | ((uint32_t)__bfloat16_as_ushort(h[3]) << 16);
+        *reinterpret_cast<uint2*>(planes + ((long)s * R + row) * Kpad + k0 + part * 4) = pk;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// exact 2^e in float32 (0 below the normal range)
+__device__ __forceinline__ float pow2f(int e) {
+  if (e < -126) return 0.0f;
+  if (e > 127) e = 127;
+  return __int_as_float((e + 127) << 23);
+}
+
+// ------------------------------------------------------- double-float helpers
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  float s = __fadd_rn(hi, x);
+  float bb = __fsub_rn(s, hi);
+  float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  err = __fadd_rn(err, lo);
+  float s2 = __fadd_rn(s, err);
+  lo = __fsub_rn(err, __fsub_rn(s2, s));
+  hi = s2;
+}
+
+// ------------------------------------------------------------- GEMM kernel
+struct GemmParams {
+  int mode;
+  int nkb;          // k blocks per segment (Kpad / 64)
+  int ntm, ntn;     // tiles along rows / columns
+  int njobs;
+  const int* exps;  // row exponents of the planes
+  // pair mode
+  const int2* pairs;
+  int np, na, energy_only;
+  double* nu_out;   // [slot][np][np]
+  // plain mode: C[m][n] = A[m] . B[n] (rows M x N), exps of A and B separately
+  int M, N;
+  const int* exps_b;
+  double* c_out;
+  long ldc;
+  // syrk mode
+  int nv, nr, nsplit;
+  const double* seg_sign;  // [nr]
+  double* dpart;           // [nsplit][nv][nv]
+  int* err;
+};
+
+template <int BN>
+__device__ __forceinline__ bool decode_job(const GemmParams& P, int job, int* slot, int* mt, int* nt) {
+  if (P.mode == MODE_PAIR) {
+    const int per = P.ntm * P.ntn;
+    *slot = job / per;
+    const int rem = job % per;
+    *mt = rem / P.ntn;
+    *nt = rem % P.ntn;
+    const int r0 = *mt * BM, c0 = *nt * BN;
+    if (r0 + BM <= P.na && c0 + BN <= P.na) return false;  // active x active only
+    if (P.energy_only && (r0 + BM <= P.na || c0 + BN <= P.na)) return false;
+    return true;
+  }
+  if (P.mode == MODE_PLAIN) {
+    *slot = 0;
+    *mt = job / P.ntn;
+    *nt = job % P.ntn;
+    return true;
+  }
+  // syrk: upper tiles only (some f >= e inside), all splits
+  int per = 0;
+  for (int m = 0; m < P.ntm; ++m) per += P.ntn - (m * BM) / BN;
+  *slot = job / per;  // split
+  int rem = job % per, m = 0;
+  while (rem >= P.ntn - (m * BM) / BN) {
+    rem -= P.ntn - (m * BM) / BN;
+    ++m;
+  }
+  *mt = m;
+  *nt = (m * BM) / BN + rem;
+  return true;
+}
+
+__device__ __forceinline__ void seg_range(const GemmParams& P, int split, int* r0, int* r1) {
+  if (P.mode != MODE_SYRK) {
+    *r0 = 0;
+    *r1 = 1;
+  } else {
+    *r0 = (int)((long)P.nr * split / P.nsplit);
+    *r1 = (int)((long)P.nr * (split + 1) / P.nsplit);
+  }
+}
+
+template <int KS, int BN, int STAGES>
+struct Cfg {
+  static constexpr int A_SLICE = BM * 128;
+  static constexpr int B_SLICE = BN * 128;
+  static constexpr int A_BYTES = KS * A_SLICE;
+  static constexpr int B_BYTES = KS * B_SLICE;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = 512;
+  static constexpr int SET_COLS = KS * BN;
+};
+
+template <int KS, int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                             const __grid_constant__ CUtensorMap mapB,
+                                                             GemmParams P) {
+  using C = Cfg<KS, BN, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done_bar = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&tfull[q], 1);
+      tc::mbar_init(&tempty[q], 4);
+    }
+    tc::mbar_init(done_bar, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&mapA);
+    tc::prefetch_tmap(&mapB);
+  }
+  if (warp == 1) tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int job = blockIdx.x; job < P.njobs && !*abort_flag; job += gridDim.x) {
+        int slot, mt, nt;
+        if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
+        int r0, r1;
+        seg_range(P, slot, &r0, &r1);
+        for (int r = r0; r < r1; ++r) {
+          int arow, brow;
+          if (P.mode == MODE_PAIR) {
+            const int2 pr = P.pairs[slot];
+            arow = pr.x * P.np + mt * BM;
+            brow = pr.y * P.np + nt * BN;
+          } else if (P.mode == MODE_PLAIN) {
+            arow = mt * BM;
+            brow = nt * BN;
+          } else {
+            arow = r * P.nv + mt * BM;
+            brow = r * P.nv + nt * BN;
+          }
+          for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!tc::mbar_wait(&empty[s], ph ^ 1, WAIT_LIMIT)) {
+              *abort_flag = 1;
+              atomicExch(P.err, 1);
+              break;
+            }
+            uint8_t* sa = smem + s * C::STAGE_BYTES;
+            tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+            tc::tma_load_3d(sa, &mapA, kb * BKE, arow, 0, &full[s]);
+            tc::tma_load_3d(sa + C::A_BYTES, &mapB, kb * BKE, brow, 0, &full[s]);
+          }
+          if (*abort_flag) break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    constexpr uint32_t IDESC = tc::make_idesc_bf16(BM, BN);
+    uint32_t it = 0, chunk = 0;
+    if (lane == 0) {
+      for (int job = blockIdx.x; job < P.njobs && !*abort_flag; job += gridDim.x) {
+        int slot, mt, nt;
+        if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
+        int r0, r1;
+        seg_range(P, slot, &r0, &r1);
+        for (int r = r0; r < r1 && !*abort_flag; ++r) {
+          uint32_t set = 0;
+          for (int kb = 0; kb < P.nkb; ++kb, ++it) {
+            const int kc = kb % KCHUNK_BLOCKS;
+            if (kc == 0) {
+              set = chunk & 1;
+              if (!tc::mbar_wait(&tempty[set], ((chunk >> 1) & 1) ^ 1, WAIT_LIMIT)) {
+                *abort_flag = 1;
+                atomicExch(P.err, 2);
+                break;
+              }
+              tc::tc_fence_after();
+            }
+            const int s = it % STAGES;
+            const uint32_t ph = (it / STAGES) & 1;
+            if (!tc::mbar_wait(&full[s], ph, WAIT_LIMIT)) {
+              *abort_flag = 1;
+              atomicExch(P.err, 3);
+              break;
+            }
+            tc::tc_fence_after();
+            const uint32_t a_base = tc::smem_u32(smem + s * C::STAGE_BYTES);
+            const uint32_t b_base = a_base + C::A_BYTES;
+#pragma unroll
+            for (int sa = 0; sa < KS; ++sa) {
+#pragma unroll
+              for (int sb = 0; sb < KS - sa; ++sb) {
+                const uint32_t d = tmem + set * C::SET_COLS + (sa + sb) * BN;
+#pragma unroll
+                for (int kk = 0; kk < BKE / 16; ++kk) {
+                  const uint64_t ad = tc::make_sdesc_sw128(a_base + sa * C::A_SLICE + kk * 32);
+                  const uint64_t bd = tc::make_sdesc_sw128(b_base + sb * C::B_SLICE + kk * 32);
+                  const uint32_t acc = (kc == 0 && kk == 0 && sa == 0) ? 0u : 1u;
+                  tc::mma_bf16(d, ad, bd, IDESC, acc);
+                }
+              }
+            }
+            tc::mma_commit(&empty[s]);
+            if (kc == KCHUNK_BLOCKS - 1 || kb == P.nkb - 1) {
+              tc::mma_commit(&tfull[set]);
+              ++chunk;
+            }
+          }
+        }
+      }
+      // all MMAs retired before TMEM is released
+      tc::mma_commit(done_bar);
+      tc::mbar_wait(done_bar, 0, WAIT_LIMIT);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------- merge / output warps
+    const int q = warp & 3;  // TMEM lane quadrant of this warp
+    const int row = q * 32 + lane;
+    uint32_t chunk = 0;
+    for (int job = blockIdx.x; job < P.njobs; job += gridDim.x) {
+      int slot, mt, nt;
+      if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
+      int r0, r1;
+      seg_range(P, slot, &r0, &r1);
+      float hi[BN], lo[BN];
+#pragma unroll
+      for (int c = 0; c < BN; ++c) {
+        hi[c] = 0.f;
+        lo[c] = 0.f;
+      }
+      bool failed = false;
+      for (int r = r0; r < r1 && !failed; ++r) {
+        // per-merge scale of this segment (syrk); pair mode scales at the end
+        float rowscale = 1.0f;
+        const int* ecol = nullptr;
+        if (P.mode == MODE_SYRK) {
+          const int e = mt * BM + row;
+          const int ea = (e < P.nv) ? P.exps[(long)r * P.nv + e] : -200;
+          rowscale = (float)P.seg_sign[r] * pow2f(ea);
+          ecol = P.exps + (long)r * P.nv + nt * BN;
+        }
+        const int nchunks = (P.nkb + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
+        for (int c = 0; c < nchunks; ++c) {
+          const uint32_t set = chunk & 1;
+          if (!tc::mbar_wait(&tfull[set], (chunk >> 1) & 1, WAIT_LIMIT)) {
+            *abort_flag = 1;
+            atomicExch(P.err, 4);
+            failed = true;
+            break;
+          }
+          tc::tc_fence_after();
+#pragma unroll 1
+          for (int L = 0; L < KS; ++L) {
+            const float lscale = pow2f(-12 - 7 * L);
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+              float v[16];
+              tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + set * C::SET_COLS + L * BN + c0, v);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                float sc = lscale * rowscale;
+                if (P.mode == MODE_SYRK) {
+                  const int f = nt * BN + c0 + j;
+                  const int eb = (f < P.nv) ? ecol[c0 + j] : -200;
+                  sc *= pow2f(eb);
+                }
+                df_add(hi[c0 + j], lo[c0 + j], v[j] * sc);
+              }
+            }
+          }
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&tempty[set]);
+          ++chunk;
+        }
+      }
+      if (failed) break;
+      // ------------------------------------------------------ tile output
+      if (P.mode == MODE_PAIR) {
+        const int2 pr = P.pairs[slot];
+        const int a = mt * BM + row;
+        if (a < P.np) {
+          const int ea = P.exps[(long)pr.x * P.np + a];
+          double* out = P.nu_out + ((long)slot * P.np + a) * P.np;
+#pragma unroll
+          for (int c = 0; c < BN; ++c) {
+            const int b = nt * BN + c;
+            if (b < P.np && !(a < P.na && b < P.na)) {
+              const int eb = P.exps[(long)pr.y * P.np + b];
+              out[b] = ldexp((double)hi[c] + (double)lo[c], ea + eb);
+            }
+          }
+        }
+      } else if (P.mode == MODE_PLAIN) {
+        const int m = mt * BM + row;
+        if (m < P.M) {
+          const int ea = P.exps[m];
+          double* out = P.c_out + (long)m * P.ldc;
+#pragma unroll
+          for (int c = 0; c < BN; ++c) {
+            const int n = nt * BN + c;
+            if (n < P.N) out[n] = ldexp((double)hi[c] + (double)lo[c], ea + P.exps_b[n]);
+          }
+        }
+      } else {
+        const int e = mt * BM + row;
+        if (e < P.nv) {
+          double* out = P.dpart + ((long)slot * P.nv + e) * P.nv;
+#pragma unroll
+          for (int c = 0; c < BN; ++c) {
+            const int f = nt * BN + c;
+            if (f < P.nv) out[f] = (double)hi[c] + (double)lo[c];
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 1) tc::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// --------------------------------------------- regulariser on the nu tiles
+// tau/kappa (vv) and t^{ij}_{ex} (va / av) from nu[slot][a][b], Eq. A7.
+__global__ void pair_epilogue_kernel(Geometry g, const double* __restrict__ eps, const int2* __restrict__ pairs,
+                                     const double* __restrict__ nu, double* __restrict__ tau,
+                                     double* __restrict__ kap, double* __restrict__ ts) {
+  const int slot = blockIdx.y;
+  const long n2 = (long)g.np * g.np;
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= n2) return;
+  const int a = (int)(idx / g.np), b = (int)(idx % g.np);
+  const int na = g.na, nv = g.nv;
+  const bool av = a >= na, bv = b >= na;
+  if (!av && !bv) return;
+  if (ts == nullptr && !(av && bv)) return;
+  const int2 pr = pairs[slot];
+  const int i = pr.x, j = pr.y;
+  const double* ep = eps + g.nc;
+  const double n = nu[(long)slot * n2 + idx];
+  const double delta = eps[i] + eps[j] - ep[a] - ep[b];
+  const double t = n * regularizer(delta, g.s);
+  if (av && bv) {
+    const long o = ((long)slot * nv + (a - na)) * nv + (b - na);
+    tau[o] = t;
+    kap[o] = 2.0 * n - delta * t;
+  } else if (av) {
+    ts[(((long)i * g.nh + j) * nv + (a - na)) * na + b] = t;
+  } else if (i != j) {
+    ts[(((long)j * g.nh + i) * nv + (b - na)) * na + a] = t;
+  }
+}
+
+// D[e][f] += sum_split dpart[split][min(e,f)][max(e,f)]
+__global__ void syrk_tc_reduce_kernel(int nv, int nsplit, const double* __restrict__ dpart, double* D) {
+  long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)nv * nv) return;
+  int e = (int)(idx / nv), f = (int)(idx % nv);
+  long src = e <= f ? (long)e * nv + f : (long)f * nv + e;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += dpart[(long)k * nv * nv + src];
+  D[idx] += s;
+}
+
+// ------------------------------------------------------- host side helpers
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3-D map over planes [KS][rows][Kpad] bf16, box {64, box_rows, KS}, 128B swizzle.
+int make_plane_map(CUtensorMap* map, const void* planes, int KS, long rows, int Kpad, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return DSRG_FNO_ERR_CUDA;
+  cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)KS};
+  cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)rows * Kpad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BKE, (cuuint32_t)box_rows, (cuuint32_t)KS};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(planes), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? DSRG_FNO_OK : DSRG_FNO_ERR_CUDA;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <int KS, int BN, int STAGES>
+int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kpad, GemmParams P,
+                cudaStream_t st) {
+  using C = Cfg<KS, BN, STAGES>;
+  CUtensorMap ma, mb;
+  DSRG_TRY(make_plane_map(&ma, pa, KS, rows_a, Kpad, BM));
+  DSRG_TRY(make_plane_map(&mb, pb, KS, rows_b, Kpad, BN));
+  auto kern = sliced_gemm_kernel<KS, BN, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    attr = true;
+  }
+  if (P.njobs <= 0) return DSRG_FNO_OK;
+  const int grid = std::min(P.njobs, num_sms());
+  void* tok = nullptr;
+  if (profiling()) {
+    // executed tensor-core flops: computed tiles x 2 BM BN Kpad x digit products
+    long tiles = 0;
+    if (P.mode == MODE_PAIR) {
+      const int per = P.ntm * P.ntn;
+      for (int t = 0; t < per; ++t) {
+        const int r0 = (t / P.ntn) * BM, c0 = (t % P.ntn) * BN;
+        bool skip = (r0 + BM <= P.na && c0 + BN <= P.na) || (P.energy_only && (r0 + BM <= P.na || c0 + BN <= P.na));
+        if (!skip) ++tiles;
+      }
+      tiles *= (long)(P.njobs / per);
+    } else if (P.mode == MODE_SYRK) {
+      tiles = (long)P.njobs / P.nsplit * P.nr;  // every segment of every upper tile
+    } else {
+      tiles = P.njobs;
+    }
+    const double fl = 2.0 * BM * BN * (double)Kpad * (KS * (KS + 1) / 2) * (double)tiles;
+    const char* nm = P.mode == MODE_PAIR ? "sliced_gemm_pair" : (P.mode == MODE_SYRK ? "sliced_gemm_syrk"
+                                                                                      : "sliced_gemm_plain");
+    prof_begin(nm, fl, st, &tok);
+  }
+  kern<<<grid, 192, C::SMEM, st>>>(ma, mb, P);
+  DSRG_LAUNCH_CHECK();
+  prof_end(tok, st);
+  return DSRG_FNO_OK;
+}
+
+int dispatch_gemm(int KS, const void* pa, long rows_a, const void* pb, long rows_b, int Kpad, GemmParams P,
+                  cudaStream_t st) {
+  switch (KS) {
+    case 3: return launch_gemm<3, 64, 3>(pa, rows_a, pb, rows_b, Kpad, P, st);
+    case 4: return launch_gemm<4, 64, 2>(pa, rows_a, pb, rows_b, Kpad, P, st);
+    case 5: return launch_gemm<5, 48, 2>(pa, rows_a, pb, rows_b, Kpad, P, st);
+    default: return DSRG_FNO_ERR_ARG;
+  }
+}
+
+int tile_n_for(int KS) { return KS == 5 ? 48 : 64; }
+
+}  // namespace
+
+// ------------------------------------------------------------ public (lib)
+int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
+               int* exps, cudaStream_t st) {
+  if (R <= 0) return DSRG_FNO_OK;
+  const int grid = (int)((R + 31) / 32);
+  switch (KS) {
+    case 3: slice_rows_kernel<3><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
+    case 4: slice_rows_kernel<4><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
+    case 5: slice_rows_kernel<5><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
+    default: return DSRG_FNO_ERR_ARG;
+  }
+  DSRG_LAUNCH_CHECK();
+  return DSRG_FNO_OK;
+}
+
+// nu[slot][a][b] for the listed pairs from B planes ([KS][nh*np][Kpad]).
+int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
+                     const int2* pairs, int npairs, bool energy_only, double* nu, int* err, cudaStream_t st) {
+  GemmParams P{};
+  P.mode = MODE_PAIR;
+  P.nkb = Kpad / BKE;
+  const int BN = tile_n_for(KS);
+  P.ntm = ceil_div(g.np, BM);
+  P.ntn = ceil_div(g.np, BN);
+  P.njobs = npairs * P.ntm * P.ntn;
+  P.exps = exps;
+  P.pairs = pairs;
+  P.np = g.np;
+  P.na = g.na;
+  P.energy_only = energy_only ? 1 : 0;
+  P.nu_out = nu;
+  P.err = err;
+  const long rows = (long)g.nh * g.np;
+  return dispatch_gemm(KS, planes, rows, planes, rows, Kpad, P, st);
+}
+
+int pair_epilogue(const Geometry& g, const double* eps, const int2* pairs, int npairs, const double* nu, double* tau,
+                  double* kap, double* ts, cudaStream_t st) {
+  if (npairs <= 0) return DSRG_FNO_OK;
+  const long n2 = (long)g.np * g.np;
+  dim3 grid(ceil_div(n2, 256), npairs);
+  pair_epilogue_kernel<<<grid, 256, 0, st>>>(g, eps, pairs, nu, tau, kap, ts);
+  DSRG_LAUNCH_CHECK();
+  return DSRG_FNO_OK;
+}
+
+// D += sum_r sign_r Sig_r Sig_r^T from Sig planes ([KS][nr*nv][Kpad]).
+int sliced_syrk(int KS, int nv, int nr, const __nv_bfloat16* planes, const int* exps, int Kpad, const double* sign,
+                double* dpart, int nsplit, double* D, int* err, cudaStream_t st) {
+  if (nr <= 0) return DSRG_FNO_OK;
+  GemmParams P{};
+  P.mode = MODE_SYRK;
+  P.nkb = Kpad / BKE;
+  const int BN = tile_n_for(KS);
+  P.ntm = ceil_div(nv, BM);
+  P.ntn = ceil_div(nv, BN);
+  int per = 0;
+  for (int m = 0; m < P.ntm; ++m) per += P.ntn - (m * BM) / BN;
+  P.njobs = per * nsplit;
+  P.exps = exps;
+  P.nv = nv;
+  P.nr = nr;
+  P.nsplit = nsplit;
+  P.seg_sign = sign;
+  P.dpart = dpart;
+  P.err = err;
+  const long rows = (long)nr * nv;
+  DSRG_TRY(dispatch_gemm(KS, planes, rows, planes, rows, Kpad, P, st));
+  syrk_tc_reduce_kernel<<<ceil_div((long)nv * nv, 256), 256, 0, st>>>(nv, nsplit, dpart, D);
+  DSRG_LAUNCH_CHECK();
+  return DSRG_FNO_OK;
+}
+
+// C[m][n] (ldc) = A[m] . B[n] from planes of A ([KS][M][Kpad]) and B ([KS][N][Kpad]).
+int sliced_plain_gemm(int KS, int M, int N, const __nv_bfloat16* pa, const int* ea, const __nv_bfloat16* pb,
+                      const int* eb, int Kpad, double* C, long ldc, int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return DSRG_FNO_OK;
+  GemmParams P{};
+  P.mode = MODE_PLAIN;
+  P.nkb = Kpad / BKE;
+  const int BN = tile_n_for(KS);
+  P.ntm = ceil_div(M, BM);
+  P.ntn = ceil_div(N, BN);
+  P.njobs = P.ntm * P.ntn;
+  P.exps = ea;
+  P.exps_b = eb;
+  P.M = M;
+  P.N = N;
+  P.c_out = C;
+  P.ldc = ldc;
+  P.err = err;
+  return dispatch_gemm(KS, pa, M, pb, N, Kpad, P, st);
+}
+
+}  // namespace dsrg

@@ -1,0 +1,91 @@
+"""Fast form (exact bf16 digit planes on tcgen05) against the FP64 oracle.
+
+Tolerances of the fast form: |dE| <= 1e-7 E_h, max |dON| <= 1e-8, identical
+N'.  D_vv elements within 1e-9 of max |D|; correction within 1e-7 E_h.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import make_problem, workload, CUTS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2312_07008_gb300 as pkg  # noqa: E402
+from test_gpu_parity import gpu_solve  # noqa: E402
+
+E_TOL, ON_TOL = 1e-7, 1e-8
+
+
+def compare_fast(p, cuts, ks=0):
+    ref = O.solve(p, cuts=cuts)
+    gp = pkg.problem_from_synth(p, "cuda", pkg.SLICED_BF16, ks)
+    nv = p.nvir
+    d = torch.empty((nv, nv), dtype=torch.float64, device="cuda")
+    e2 = pkg.dsrg_fno_vv_opdm(gp, d)
+    on = torch.empty(nv, dtype=torch.float64, device="cuda")
+    no = torch.empty((nv, nv), dtype=torch.float64, device="cuda")
+    errs = dict(e2=abs(e2 - ref["e2"]), d=float(np.max(np.abs(d.cpu().numpy() - ref["dvv"]))))
+    errs["e2_only"] = abs(pkg.dsrg_fno_pt2_energy(gp) - ref["e2"])
+    for c in cuts:
+        k = pkg.dsrg_fno_truncate(nv, d, pkg.MODE_PO, c, 0.01, on, no)
+        de, _ = pkg.dsrg_fno_discarded_correction(gp, k, no, e2_mo=e2)
+        r = ref["cuts"][c]
+        errs[f"nkept{c}"] = (k, r["nkept"])
+        errs[f"de{c}"] = abs(de - r["de"])
+    errs["on"] = float(np.max(np.abs(on.cpu().numpy() - ref["ons"])))
+    return errs, ref
+
+
+def check(errs, ref, cuts):
+    print(errs)
+    assert errs["e2"] <= E_TOL and errs["e2_only"] <= E_TOL
+    assert errs["on"] <= ON_TOL
+    assert errs["d"] <= 1e-9 * np.max(np.abs(ref["dvv"]))
+    for c in cuts:
+        k, kr = errs[f"nkept{c}"]
+        assert k == kr
+        assert errs[f"de{c}"] <= E_TOL
+
+
+def test_fast_single_reference_workload():
+    name = "sr_nocc10_nvir90_naux300"
+    errs, ref = compare_fast(workload(name), CUTS[name])
+    check(errs, ref, CUTS[name])
+
+
+def test_fast_cas6_workload():
+    name = "sa_cas6_ncore20_nvir300_naux1000"
+    errs, ref = compare_fast(workload(name), CUTS[name])
+    check(errs, ref, CUTS[name])
+
+
+@pytest.mark.parametrize("shape", [
+    dict(ncore=3, nact=2, nvir=67, naux=130, nstates=2),
+    dict(ncore=1, nact=0, nvir=5, naux=3, nstates=1),
+    dict(ncore=5, nact=5, nvir=129, naux=65, nstates=3),
+    dict(ncore=0, nact=4, nvir=40, naux=600, nstates=2),       # several 512-wide k chunks
+    dict(ncore=9, nact=3, nvir=200, naux=1100, nstates=2),
+])
+def test_fast_ragged_shapes(shape):
+    p = make_problem(seed=41, s=0.5, **shape)
+    errs, ref = compare_fast(p, (98.5, 90.0))
+    check(errs, ref, (98.5, 90.0))
+
+
+def test_fast_error_falls_with_digit_planes():
+    """Odd plane counts: the energy error falls by about 2^-14 per two planes.
+    (An even count k leaves the square d_{k/2} d_{k/2} in the first dropped
+    level, a biased term; its error is reported, not asserted.)"""
+    p = make_problem(ncore=6, nact=4, nvir=150, naux=700, seed=43, nstates=2)
+    e = {}
+    for ks in (3, 4, 5):
+        errs, _ = compare_fast(p, (98.5,), ks)
+        e[ks] = errs["e2"] + 1e-16
+    print("E errors by planes 3/4/5:", e)
+    assert e[5] < e[3] / 1000
+    assert e[5] <= E_TOL
