@@ -109,6 +109,27 @@ int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double thre
                       double degen_ratio, double* on_out, double* no_out,
                       int32_t* nkept_out, void* stream);
 
+/* dsrg_fno_truncate without any device allocation (the paper has no
+ * counterpart; this is a service for callers that cannot allocate).  Some
+ * callers cannot call cudaMalloc: a framework that owns all device memory
+ * through its own pool, or a latency-critical loop where an allocation, which
+ * may synchronise the device, is not acceptable.  This call does the same
+ * eigensolve and cut as dsrg_fno_truncate with the same arguments, but its
+ * scratch is one fixed file-scope device array of the library (4 nvir^2
+ * doubles for nvir up to 512, about 8 MB), held by every device that loads
+ * the library until the process exits.
+ *   - nvir > 512 returns DSRG_FNO_ERR_ARG (message on stderr).
+ *   - The first call on a device looks up the array's device address on that
+ *     device (set-up); make that first call before any stream capture.
+ *   - Every call on a device shares the array, which keeps the last call's
+ *     contents; each call writes every scratch word before reading it.  Calls
+ *     whose GPU work overlaps (other streams or threads) race on the array:
+ *     serialise them.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called. */
+int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_t mode, double threshold,
+                              double degen_ratio, double* on_out, double* no_out,
+                              int32_t* nkept_out, void* stream);
+
 /* Second-order correction for the discarded virtuals (scalar part of
  * Eq. 11): the kept NOs (first nkept columns of `no`, device [nvir][nvir])
  * are recanonicalised (virtual Fock block diagonal, Sec. 2), B is rotated to

@@ -19,6 +19,7 @@ EXPORTED = (
     "dsrg_fno_pt2_energy",
     "dsrg_fno_vv_opdm",
     "dsrg_fno_truncate",
+    "dsrg_fno_truncate_noalloc",
     "dsrg_fno_discarded_correction",
     "dsrg_fno_status_string",
     "dsrg_fno_release",
@@ -66,6 +67,7 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_pt2_energy.argtypes = [P, ctypes.POINTER(d), vp]
     lib.dsrg_fno_vv_opdm.argtypes = [P, vp, ctypes.POINTER(d), vp]
     lib.dsrg_fno_truncate.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
+    lib.dsrg_fno_truncate_noalloc.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_discarded_correction.argtypes = [P, i32, vp, ctypes.POINTER(d), ctypes.POINTER(d),
                                                   ctypes.POINTER(d), vp, vp]
     lib.dsrg_fno_status_string.argtypes = [ctypes.c_int]
@@ -81,7 +83,8 @@ def load(path: str = LIB_PATH):
                                            ctypes.POINTER(d)]
     lib.dsrg_fno_launch_count.argtypes = [i32]
     lib.dsrg_fno_launch_count.restype = ctypes.c_int64
-    for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_truncate", "dsrg_fno_discarded_correction"):
+    for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_truncate", "dsrg_fno_truncate_noalloc",
+              "dsrg_fno_discarded_correction"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -147,6 +150,15 @@ def dsrg_fno_truncate(nvir, dvv, mode, threshold, degen_ratio, on_out, no_out, s
     _check("dsrg_fno_truncate", load().dsrg_fno_truncate(nvir, _ptr(dvv), mode, float(threshold),
                                                         float(degen_ratio), _ptr(on_out), _ptr(no_out),
                                                         ctypes.byref(k), _stream(stream)))
+    return k.value
+
+
+def dsrg_fno_truncate_noalloc(nvir, dvv, mode, threshold, degen_ratio, on_out, no_out, stream=None) -> int:
+    """dsrg_fno_truncate that allocates nothing on the device (nvir <= 512)."""
+    k = ctypes.c_int32()
+    _check("dsrg_fno_truncate_noalloc",
+           load().dsrg_fno_truncate_noalloc(nvir, _ptr(dvv), mode, float(threshold), float(degen_ratio),
+                                            _ptr(on_out), _ptr(no_out), ctypes.byref(k), _stream(stream)))
     return k.value
 
 

@@ -1,0 +1,85 @@
+// Natural orbitals and truncation without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a host framework that owns all device
+// memory through its own pool and forbids stray allocations, or a latency-
+// critical loop where an allocation (which may synchronise the whole device)
+// is not acceptable.  dsrg_fno_truncate_noalloc serves them with the same
+// eigensolver and cut as dsrg_fno_truncate, using as scratch one file-scope
+// device array of fixed size instead of the library's workspace.
+#include <stdio.h>
+
+#include <mutex>
+
+#include "kernels.h"
+
+namespace dsrg {
+
+// Largest nvir the array serves: A, V and the Jacobi work (4 n^2 doubles),
+// then status, N' and the sort ranks (n + 8 ints) in its tail.
+constexpr int NOALLOC_NVIR_MAX = 512;
+constexpr size_t NOALLOC_DOUBLES =
+    4 * (size_t)NOALLOC_NVIR_MAX * NOALLOC_NVIR_MAX + 8 + (NOALLOC_NVIR_MAX + 8 + 1) / 2 + 1;
+
+// Held by every device that loads the library, until the process exits.
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+static std::mutex g_noalloc_setup_mutex;
+static double* g_noalloc_ptr[64] = {};
+
+// Device address of the array on the current device (host code cannot use
+// the symbol itself: it names a host-side stand-in).
+static int noalloc_scratch(double** out) {
+  int dev = 0;
+  DSRG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return DSRG_FNO_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_setup_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      fprintf(stderr, "dsrg_fno_truncate_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return DSRG_FNO_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return DSRG_FNO_OK;
+}
+
+}  // namespace dsrg
+
+using namespace dsrg;
+
+extern "C" int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_t mode, double threshold,
+                                         double degen_ratio, double* on_out, double* no_out, int32_t* nkept_out,
+                                         void* stream) {
+  if (nvir > NOALLOC_NVIR_MAX) {
+    fprintf(stderr, "dsrg_fno_truncate_noalloc: nvir = %d exceeds the fixed scratch limit of %d\n", nvir,
+            NOALLOC_NVIR_MAX);
+    return DSRG_FNO_ERR_ARG;
+  }
+  if (nvir <= 0 || !dvv || !on_out || !no_out || !nkept_out) return DSRG_FNO_ERR_ARG;
+  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* base = nullptr;
+  DSRG_TRY(noalloc_scratch(&base));
+  const size_t n2 = (size_t)nvir * nvir;
+  double* A = base;
+  double* V = A + n2;
+  double* work = V + n2;  // 2 n^2 + 8
+  int* ib = reinterpret_cast<int*>(work + 2 * n2 + 8);
+  int* status = ib;
+  int* nk = ib + 1;
+  int* rank = ib + 8;
+  // Every scratch word read below is first written by this call: A is a copy
+  // of dvv, the Jacobi sets V to the identity and zeroes its status word.
+  DSRG_CUDA(cudaMemcpyAsync(A, dvv, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  DSRG_TRY(eig_sym_jacobi(nvir, A, V, work, status, 60, st));
+  DSRG_TRY(eig_sort(nvir, A, V, on_out, no_out, rank, true, true, st));
+  DSRG_TRY(truncate_ons(nvir, on_out, mode, threshold, degen_ratio, nk, st));
+  int h = 0;
+  DSRG_CUDA(cudaMemcpyAsync(&h, nk, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  *nkept_out = h;
+  return DSRG_FNO_OK;
+}
