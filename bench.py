@@ -233,6 +233,12 @@ def main():
     launches = pkg.dsrg_fno_launch_count()
     ms = ev0.elapsed_time(ev1)
     clocks = clk.stop()
+    phases = {}
+    for nm in ("sliced_gemm_pair", "sliced_gemm_syrk", "sliced_gemm_plain", "phase_stage_b", "phase_pair_epilogue",
+               "phase_dress", "phase_stage_sig", "phase_small_terms", "phase_no_eigen", "phase_density_eigen",
+               "phase_recanon_and_rotate"):
+        t_ms, n_l, _ = pkg.dsrg_fno_profile_query(nm)
+        phases[nm] = {"ms_per_step": t_ms / args.steps, "launches_or_calls": n_l}
     pair_ms, pair_n, pair_fl = pkg.dsrg_fno_profile_query("sliced_gemm_pair")
     syrk_ms, syrk_n, syrk_fl = pkg.dsrg_fno_profile_query("sliced_gemm_syrk")
     plain_ms, plain_n, plain_fl = pkg.dsrg_fno_profile_query("sliced_gemm_plain")
@@ -319,6 +325,7 @@ def main():
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "phases": phases,
         "clocks": clocks,
         "fp64_form": fp64,
         "result": {"e2": res["e2"], **{f"nkept_{c}": res[c][0] for c in cuts}, **{f"de_{c}": res[c][1] for c in cuts}},

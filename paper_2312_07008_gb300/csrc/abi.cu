@@ -220,6 +220,7 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
   const int na = g.na;
   DressAux aux{};
   if (na > 0) {
+    DSRG_PHASE("phase_density_eigen", st);
     const int ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
     DSRG_CUDA(cudaMemcpyAsync(W.g1A, gamma1, sizeof(double) * na * na, cudaMemcpyDeviceToDevice, st));
     DSRG_TRY(eig_sym_jacobi(na, W.g1A, W.g1V, W.g1W, W.status, 60, st));
@@ -237,6 +238,7 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
   if (W.ks) {
     // digit planes of B: rows (hole, particle), contraction over Q
     const long rows = (long)g.nh * g.np;
+    DSRG_PHASE("phase_stage_b", st);
     DSRG_TRY(slice_rows(W.ks, B, rows, g.nq, 1, rows, W.kpad_q, W.planes_b, W.exps_b, st));
   }
   for (size_t bi = 0; bi < P.batches.size(); ++bi) {
@@ -245,16 +247,21 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
     if (W.ks) {
       DSRG_TRY(sliced_pair_gemm(W.ks, g, W.planes_b, W.exps_b, W.kpad_q, W.pairs + b.pair_begin, b.npairs,
                                 ts == nullptr, W.nu, W.err, st));
+      DSRG_PHASE("phase_pair_epilogue", st);
       DSRG_TRY(pair_epilogue(g, eps, W.pairs + b.pair_begin, b.npairs, W.nu, W.tau, W.kap, ts, st));
     } else {
       DSRG_TRY(pair_gemm_f64(g, B, eps, W.pairs + b.pair_begin, b.npairs, W.tau, W.kap, ts, st));
     }
-    DSRG_TRY(dress_f64(g, W.desc + b.desc_begin, b.ndesc, aux, W.tau, W.kap, W.sig, W.sig_sign, W.e_part, want_d,
-                       st));
+    {
+      DSRG_PHASE("phase_dress", st);
+      DSRG_TRY(dress_f64(g, W.desc + b.desc_begin, b.ndesc, aux, W.tau, W.kap, W.sig, W.sig_sign, W.e_part,
+                         want_d, st));
+    }
     DSRG_TRY(ordered_sum(W.e_part, (long)b.ndesc * ntd * ntd, W.e_acc, bi > 0, st));
     if (want_d) {
       if (W.ks) {
         const long rows = (long)b.ndesc * g.nv;
+        DSRG_PHASE("phase_stage_sig", st);
         DSRG_TRY(slice_rows(W.ks, W.sig, rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, st));
         DSRG_TRY(sliced_syrk(W.ks, g.nv, b.ndesc, W.planes_s, W.exps_s, W.kpad_v, W.sig_sign, W.dpart, W.nsplit, D,
                              W.err, st));
@@ -479,6 +486,7 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   DSRG_CUDA(cudaMemsetAsync(dvv_out, 0, nv2 * sizeof(double), st));
   DSRG_TRY(run_pass(g, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, P, W, true, dvv_out, st));
   if (g.na > 0 || prob->f_hp) {
+    DSRG_PHASE("phase_small_terms", st);
     DSRG_TRY(t1_amplitudes(g, g.na ? W.ts : nullptr, prob->eps, prob->f_hp, prob->gamma1, t1, st));
     DSRG_TRY(small_terms_f64(g, g.na ? W.ts : nullptr, t1, prob->gamma1, prob->lambda2, dvv_out, work, st));
   }
@@ -514,6 +522,7 @@ int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double thre
   int* nk = ib + 1;
   int* rank = ib + 8;
   DSRG_CUDA(cudaMemcpyAsync(A, dvv, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  DSRG_PHASE("phase_no_eigen", st);
   int s = eig_sym_jacobi(nvir, A, V, work, status, 60, st);
   if (s) return s;
   DSRG_TRY(eig_sort(nvir, A, V, on_out, no_out, rank, true, true, st));
@@ -575,6 +584,8 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
   double e_f = 0.0;
   if (nk > 0) {
     // F' = Vk^T diag(eps_v) Vk, recanonicalised: F' W = W eps'
+    {
+    DSRG_PHASE("phase_recanon_and_rotate", st);
     const double* ev = prob->eps + g.nh;
     DSRG_TRY(scale_rows(nv, nk, nv, ev, no, Wt, st));
     DSRG_TRY(gemm_f64(nk, nk, nv, 1.0, no, nv, false, Wt, nk, false, 0.0, F, nk, 1, 0, 0, 0, st));
@@ -601,6 +612,7 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
     } else {
       DSRG_TRY(gemm_f64((int)rows, nk, nv, 1.0, prob->B_hp + g.na, g.np, true, U, nk, false, 0.0, Bf + g.na, gf.np,
                         1, 0, 0, 0, st));
+    }
     }
     DSRG_CUDA(cudaMemcpyAsync(epsf, prob->eps, sizeof(double) * g.nh, cudaMemcpyDeviceToDevice, st));
     DSRG_CUDA(cudaMemcpyAsync(epsf + g.nh, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));

@@ -35,6 +35,17 @@ void count_launch();
 bool profiling();
 void prof_begin(const char* name, double flops, cudaStream_t st, void** token);
 void prof_end(void* token, cudaStream_t st);
+// Scoped timing of a phase of a call (recorded only while profiling).
+struct PhaseTimer {
+  void* tok = nullptr;
+  cudaStream_t st;
+  PhaseTimer(const char* name, cudaStream_t s) : st(s) { prof_begin(name, 0.0, s, &tok); }
+  ~PhaseTimer() { prof_end(tok, st); }
+};
+#define DSRG_CAT2(a, b) a##b
+#define DSRG_CAT(a, b) DSRG_CAT2(a, b)
+#define DSRG_PHASE(name, st) PhaseTimer DSRG_CAT(phase_timer_, __LINE__)(name, st)
+
 #define DSRG_LAUNCH_CHECK() \
   do {                      \
     count_launch();         \

@@ -3,16 +3,17 @@
 //
 // Staging.  Each float64 row v[k] (k = contraction index) gets a power-of-two
 // scale 2^e_row with max_k |v| < 2^e_row, and the scaled value x = v 2^-e_row
-// is rounded to X = round(x 2^F), F = 6 + 7 (KS - 1), then written in balanced
-// radix 128:  X = sum_s d_s 128^(KS-1-s),  d_s integer in [-64, 64], exact in
-// bfloat16.  Hence x = 2^-6 sum_s d_s 2^-7s up to 2^-(F+1).
+// is rounded to X = round(x 2^F), F = 7 + 8 (KS - 1), then written in balanced
+// radix 256:  X = sum_s d_s 256^(KS-1-s),  d_s integer in [-128, 128], exact in
+// bfloat16 (8 significant bits).  Hence x = 2^-7 sum_s d_s 2^-8s up to 2^-(F+1).
 //
-// Products.  For two rows a, b:  x_a . x_b = 2^-12 sum_L 2^-7L S_L with the
+// Products.  For two rows a, b:  x_a . x_b = 2^-14 sum_L 2^-8L S_L with the
 // level sums S_L = sum_{s+t=L} sum_k d_s(a,k) d_t(b,k).  Only levels
 // L <= KS-1 are formed (triangular truncation, KS(KS+1)/2 digit products).
-// Every digit product is an integer of magnitude <= 2^12, so a level sum over
-// a chunk of 512 k-values holds at most (L+1) 2^21 <= 2^24 in magnitude and
-// the float32 accumulator of the tensor core represents it exactly.
+// Every digit product is an integer of magnitude <= 2^14, so a level sum over
+// a chunk of 192 k-values holds at most (L+1) 192 2^14 < 2^24 in magnitude
+// (L <= 4) and the float32 accumulator of the tensor core represents it
+// exactly.
 //
 // Kernel.  Persistent, warp-specialised: warp 0 issues TMA loads of all KS
 // planes of a 64-wide k block (128-byte swizzle) into a 2-3 stage ring, warp 1
@@ -32,7 +33,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BKE = 64;            // k elements per block (128 bytes of bf16)
-constexpr int KCHUNK_BLOCKS = 8;   // 512 k-values per exact level sum
+constexpr int KCHUNK_BLOCKS = 3;   // 192 k-values per exact level sum
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
 
 enum { MODE_PAIR = 0, MODE_SYRK = 1, MODE_PLAIN = 2 };
@@ -47,21 +48,21 @@ __device__ __forceinline__ int row_exponent(double maxabs) {
 
 template <int KS>
 __device__ __forceinline__ void digits_of(double v, int e_row, int* d) {
-  constexpr int F = 6 + 7 * (KS - 1);
+  constexpr int F = 7 + 8 * (KS - 1);
   long long b = __double_as_longlong(v);
   int E = (int)((b >> 52) & 0x7FF);
   long long X = 0;
   if (E != 0) {
     long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-    int sh = 1075 - E - F + e_row;  // >= 5 for KS <= 7 because |v| < 2^e_row
+    int sh = 1075 - E - F + e_row;  // >= 14 for KS <= 5 because |v| < 2^e_row
     if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
     if (b < 0) X = -X;
   }
 #pragma unroll
   for (int s = KS - 1; s >= 1; --s) {
-    long long r = ((X + 64) & 127) - 64;
+    long long r = ((X + 128) & 255) - 128;
     d[s] = (int)r;
-    X = (X - r) >> 7;
+    X = (X - r) >> 8;
   }
   d[0] = (int)X;
 }
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           tc::tc_fence_after();
 #pragma unroll 1
           for (int L = 0; L < KS; ++L) {
-            const float lscale = pow2f(-12 - 7 * L);
+            const float lscale = pow2f(-14 - 8 * L);
 #pragma unroll
             for (int c0 = 0; c0 < BN; c0 += 16) {
               float v[16];
