@@ -207,8 +207,11 @@ def main():
     def step(prob):
         e2 = pkg.dsrg_fno_vv_opdm(prob, d)
         res = {"e2": e2}
-        for c in cuts:
-            k = pkg.dsrg_fno_truncate(nv, d, pkg.MODE_PO, c, 0.01, on, no)
+        for i, c in enumerate(cuts):
+            if i == 0:   # NOs once, then every cut of the same ONs
+                k = pkg.dsrg_fno_truncate(nv, d, pkg.MODE_PO, c, 0.01, on, no)
+            else:
+                k = pkg.dsrg_fno_cut(nv, on, pkg.MODE_PO, c, 0.01)
             de, ef = pkg.dsrg_fno_discarded_correction(prob, k, no, e2_mo=e2)
             res[c] = (k, de)
         return res

@@ -109,6 +109,13 @@ int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double thre
                       double degen_ratio, double* on_out, double* no_out,
                       int32_t* nkept_out, void* stream);
 
+/* The truncation of dsrg_fno_truncate applied to ONs already computed (for
+ * further cuts of the same NOs, e.g. p_o = 98 % and 99 %).
+ *   ons  device [nvir], descending (as written by dsrg_fno_truncate).
+ *   mode, threshold, degen_ratio, nkept_out: as in dsrg_fno_truncate. */
+int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold, double degen_ratio,
+                 int32_t* nkept_out, void* stream);
+
 /* dsrg_fno_truncate without any device allocation (the paper has no
  * counterpart; this is a service for callers that cannot allocate).  Some
  * callers cannot call cudaMalloc: a framework that owns all device memory

@@ -20,6 +20,7 @@ EXPORTED = (
     "dsrg_fno_vv_opdm",
     "dsrg_fno_truncate",
     "dsrg_fno_truncate_noalloc",
+    "dsrg_fno_cut",
     "dsrg_fno_discarded_correction",
     "dsrg_fno_status_string",
     "dsrg_fno_release",
@@ -68,6 +69,7 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_vv_opdm.argtypes = [P, vp, ctypes.POINTER(d), vp]
     lib.dsrg_fno_truncate.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_truncate_noalloc.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
+    lib.dsrg_fno_cut.argtypes = [i32, vp, i32, d, d, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_discarded_correction.argtypes = [P, i32, vp, ctypes.POINTER(d), ctypes.POINTER(d),
                                                   ctypes.POINTER(d), vp, vp]
     lib.dsrg_fno_status_string.argtypes = [ctypes.c_int]
@@ -84,7 +86,7 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_launch_count.argtypes = [i32]
     lib.dsrg_fno_launch_count.restype = ctypes.c_int64
     for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_truncate", "dsrg_fno_truncate_noalloc",
-              "dsrg_fno_discarded_correction"):
+              "dsrg_fno_cut", "dsrg_fno_discarded_correction"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -150,6 +152,14 @@ def dsrg_fno_truncate(nvir, dvv, mode, threshold, degen_ratio, on_out, no_out, s
     _check("dsrg_fno_truncate", load().dsrg_fno_truncate(nvir, _ptr(dvv), mode, float(threshold),
                                                         float(degen_ratio), _ptr(on_out), _ptr(no_out),
                                                         ctypes.byref(k), _stream(stream)))
+    return k.value
+
+
+def dsrg_fno_cut(nvir, ons, mode, threshold, degen_ratio, stream=None) -> int:
+    """N' for ONs already on the device (further cuts of the same NOs)."""
+    k = ctypes.c_int32()
+    _check("dsrg_fno_cut", load().dsrg_fno_cut(nvir, _ptr(ons), mode, float(threshold), float(degen_ratio),
+                                              ctypes.byref(k), _stream(stream)))
     return k.value
 
 

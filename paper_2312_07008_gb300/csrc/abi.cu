@@ -473,8 +473,14 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, device_budget() + ws.cap / 2), P);
   const int nsplit = nsplit_for(g.nv, P.max_desc);
   const size_t small = small_terms_work_doubles(g.nc, g.na, g.nv);
+  const int kmax = small_terms_kmax(g.nc, g.na);
+  const bool small_fast = ks > 0 && kmax >= SLICED_MIN_K;
+  const size_t small_fast_bytes =
+      small_fast ? ws_bytes(2 * (size_t)ks * g.nv * pad64(kmax), 2) + ws_bytes(2 * (size_t)g.nv, sizeof(int)) +
+                       doubles((size_t)g.nv * g.nv) + ws_bytes(8, sizeof(int))
+                 : 0;
   size_t need = ws_bytes(8, sizeof(int)) + pass_bytes(g, P, true, nsplit, ks) + doubles((size_t)g.nh * g.nv) +
-                doubles(small + 1);
+                doubles(small + 1) + small_fast_bytes;
   DSRG_TRY(ws_reserve(ws, need));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
@@ -482,13 +488,21 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   DSRG_TRY(carve_pass(ws, g, P, true, nsplit, ks, W, st));
   double* t1 = ws_take<double>(ws, (size_t)g.nh * g.nv);
   double* work = ws_take<double>(ws, small + 1);
+  SmallFast sf{0, nullptr, nullptr, nullptr, nullptr};
+  if (small_fast) {
+    sf.ks = ks;
+    sf.planes = ws_take<__nv_bfloat16>(ws, 2 * (size_t)ks * g.nv * pad64(kmax));
+    sf.exps = ws_take<int>(ws, 2 * (size_t)g.nv);
+    sf.cbuf = ws_take<double>(ws, (size_t)g.nv * g.nv);
+    sf.err = W.err;
+  }
   const size_t nv2 = (size_t)g.nv * g.nv;
   DSRG_CUDA(cudaMemsetAsync(dvv_out, 0, nv2 * sizeof(double), st));
   DSRG_TRY(run_pass(g, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, P, W, true, dvv_out, st));
   if (g.na > 0 || prob->f_hp) {
     DSRG_PHASE("phase_small_terms", st);
     DSRG_TRY(t1_amplitudes(g, g.na ? W.ts : nullptr, prob->eps, prob->f_hp, prob->gamma1, t1, st));
-    DSRG_TRY(small_terms_f64(g, g.na ? W.ts : nullptr, t1, prob->gamma1, prob->lambda2, dvv_out, work, st));
+    DSRG_TRY(small_terms_f64(g, g.na ? W.ts : nullptr, t1, prob->gamma1, prob->lambda2, dvv_out, work, sf, st));
   }
   DSRG_TRY(symmetrize(g.nv, dvv_out, st));
   DSRG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
@@ -527,6 +541,23 @@ int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double thre
   if (s) return s;
   DSRG_TRY(eig_sort(nvir, A, V, on_out, no_out, rank, true, true, st));
   DSRG_TRY(truncate_ons(nvir, on_out, mode, threshold, degen_ratio, nk, st));
+  int h = 0;
+  DSRG_CUDA(cudaMemcpyAsync(&h, nk, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  *nkept_out = h;
+  return DSRG_FNO_OK;
+}
+
+int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold, double degen_ratio,
+                 int32_t* nkept_out, void* stream) {
+  if (nvir <= 0 || !ons || !nkept_out || !is_device_ptr(ons)) return DSRG_FNO_ERR_ARG;
+  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  DSRG_TRY(ws_reserve(ws, ws_bytes(8, sizeof(int))));
+  int* nk = ws_take<int>(ws, 8);
+  DSRG_TRY(truncate_ons(nvir, ons, mode, threshold, degen_ratio, nk, st));
   int h = 0;
   DSRG_CUDA(cudaMemcpyAsync(&h, nk, sizeof(int), cudaMemcpyDeviceToHost, st));
   DSRG_CUDA(cudaStreamSynchronize(st));

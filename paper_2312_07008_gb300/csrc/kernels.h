@@ -73,8 +73,18 @@ int ordered_sum(const double* x, long n, double* out, bool accumulate, cudaStrea
 int t1_amplitudes(const Geometry& g, const double* ts, const double* eps, const double* f_hp,
                   const double* g1, double* t1, cudaStream_t st);
 size_t small_terms_work_doubles(int nc, int na, int nv);
+int small_terms_kmax(int nc, int na);
+// Buffers of the tensor-core path of the small terms (ks = 0: float64 only).
+struct SmallFast {
+  int ks;
+  __nv_bfloat16* planes;  // 2 * ks * nv * pad64(kmax)
+  int* exps;              // 2 * nv
+  double* cbuf;           // nv * nv
+  int* err;
+};
+constexpr int SLICED_MIN_K = 1024;
 int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1,
-                    const double* l2, double* D, double* work, cudaStream_t st);
+                    const double* l2, double* D, double* work, const SmallFast& F, cudaStream_t st);
 
 // Fast form: exact bf16 digit planes on tcgen05 (sliced.cu)
 int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,

@@ -247,9 +247,28 @@ int t1_amplitudes(const Geometry& g, const double* ts, const double* eps, const 
   return DSRG_FNO_OK;
 }
 
+__global__ void axpy_kernel(long n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fma(a, x[i], y[i]);
+}
+
+// Largest K of any term part (the contraction length of its GEMM).
+int small_terms_kmax(int nc, int na) {
+  int kmax = 0;
+  for (int t = 0; t < NTERMS; ++t) {
+    int K;
+    double c;
+    term_shape(t, nc, na, &K, &c);
+    kmax = K > kmax ? K : kmax;
+  }
+  return kmax;
+}
+
 // D += terms 1-3, 6, 8-12.  work: small_terms_work_doubles() doubles.
+// With F.ks > 0, the GEMMs with K >= SLICED_MIN_K run on the tensor cores
+// (digit planes of X and Y, exact level sums), the rest in float64.
 int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1, const double* l2,
-                    double* D, double* work, cudaStream_t st) {
+                    double* D, double* work, const SmallFast& F, cudaStream_t st) {
   SI S{g.nc, g.na, g.nv, g.nh, ts, t1, g1, l2};
   for (int term = 0; term < NTERMS; ++term) {
     if (g.na == 0 && term != T1_CORE) continue;
@@ -262,7 +281,19 @@ int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const
     long n = (long)g.nv * K;
     build_kernel<<<ceil_div(n, 256), 256, 0, st>>>(S, term, K, X, Y);
     DSRG_LAUNCH_CHECK();
-    DSRG_TRY(gemm_f64(g.nv, g.nv, K, coef, X, K, true, Y, K, true, 1.0, D, g.nv, 1, 0, 0, 0, st));
+    if (F.ks > 0 && K >= SLICED_MIN_K) {
+      const int kp = pad64(K);
+      __nv_bfloat16* px = F.planes;
+      __nv_bfloat16* py = F.planes + (size_t)F.ks * g.nv * kp;
+      DSRG_TRY(slice_rows(F.ks, X, g.nv, K, K, 1, kp, px, F.exps, st));
+      DSRG_TRY(slice_rows(F.ks, Y, g.nv, K, K, 1, kp, py, F.exps + g.nv, st));
+      DSRG_TRY(sliced_plain_gemm(F.ks, g.nv, g.nv, px, F.exps, py, F.exps + g.nv, kp, F.cbuf, g.nv, F.err, st));
+      const long n2 = (long)g.nv * g.nv;
+      axpy_kernel<<<ceil_div(n2, 256), 256, 0, st>>>(n2, coef, F.cbuf, D);
+      DSRG_LAUNCH_CHECK();
+    } else {
+      DSRG_TRY(gemm_f64(g.nv, g.nv, K, coef, X, K, true, Y, K, true, 1.0, D, g.nv, 1, 0, 0, 0, st));
+    }
   }
   return DSRG_FNO_OK;
 }
