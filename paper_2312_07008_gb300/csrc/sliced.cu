@@ -10,16 +10,21 @@
 // Products.  For two rows a, b:  x_a . x_b = 2^-14 sum_L 2^-8L S_L with the
 // level sums S_L = sum_{s+t=L} sum_k d_s(a,k) d_t(b,k).  Only levels
 // L <= KS-1 are formed (triangular truncation, KS(KS+1)/2 digit products).
-// Every digit product is an integer of magnitude <= 2^14, so a level sum over
-// a chunk of 192 k-values holds at most (L+1) 192 2^14 < 2^24 in magnitude
-// (L <= 4) and the float32 accumulator of the tensor core represents it
-// exactly.
+// Every digit product is an integer of magnitude <= 2^14, so the level sums
+// S_0, S_1, S_2 over a chunk of 320 k-values stay below 3 * 320 * 2^14 < 2^24
+// in magnitude and the float32 accumulator of the tensor core holds them
+// exactly; they are merged after every chunk.  The levels L >= 3 carry
+// weights 2^-38 and smaller, so their float32 rounding (about 2^-24 of the
+// level) stays far below the digit truncation: they accumulate over the whole
+// contraction in TMEM and are merged once per tile (per segment in the
+// rank-K update).
 //
 // Kernel.  Persistent, warp-specialised: warp 0 issues TMA loads of all KS
 // planes of a 64-wide k block (128-byte swizzle) into a 2-3 stage ring, warp 1
-// issues tcgen05.mma into per-level TMEM accumulators (two sets, double
-// buffered), warps 2-5 drain each finished chunk with tcgen05.ld and add
-// 2^-7L S_L into a float32-pair (double-float) accumulator per element.  At the
+// issues tcgen05.mma into per-level TMEM accumulators (levels 0-2 double
+// buffered per chunk, levels >= 3 double buffered per segment), warps 2-5
+// drain them with tcgen05.ld and add 2^-14-8L S_L into a float32-pair
+// (double-float) accumulator per element.  At the
 // end of a tile the float64 result is written out.  Every mbarrier wait is
 // bounded; on expiry the kernel records the failure and leaves.
 #include <cuda.h>
@@ -33,7 +38,8 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BKE = 64;            // k elements per block (128 bytes of bf16)
-constexpr int KCHUNK_BLOCKS = 3;   // 192 k-values per exact level sum
+constexpr int KCHUNK_BLOCKS = 5;   // 320 k-values per exact sum of levels 0, 1, 2
+constexpr int NEXACT = 3;          // levels kept exact per chunk
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
 
 enum { MODE_PAIR = 0, MODE_SYRK = 1, MODE_PLAIN = 2 };
@@ -228,7 +234,10 @@ struct Cfg {
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr int TMEM_COLS = 512;
-  static constexpr int SET_COLS = KS * BN;
+  static constexpr int SET_COLS = NEXACT * BN;              // exact levels of one chunk
+  static constexpr int TAIL_BASE = 2 * SET_COLS;             // lower levels of one segment
+  static constexpr int TAIL_COLS = (KS - NEXACT) * BN;
+  static_assert(2 * SET_COLS + 2 * (TAIL_COLS > 0 ? TAIL_COLS : 0) <= TMEM_COLS, "TMEM budget");
 };
 
 template <int KS, int BN, int STAGES>
@@ -242,7 +251,9 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
-  uint64_t* done_bar = tempty + 2;
+  uint64_t* lfull = tempty + 2;   // low-order levels of a segment ready
+  uint64_t* lempty = lfull + 2;   // ... drained
+  uint64_t* done_bar = lempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -255,6 +266,8 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
     for (int q = 0; q < 2; ++q) {
       tc::mbar_init(&tfull[q], 1);
       tc::mbar_init(&tempty[q], 4);
+      tc::mbar_init(&lfull[q], 1);
+      tc::mbar_init(&lempty[q], 4);
     }
     tc::mbar_init(done_bar, 1);
     *abort_flag = 0;
@@ -312,7 +325,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     constexpr uint32_t IDESC = tc::make_idesc_bf16(BM, BN);
-    uint32_t it = 0, chunk = 0;
+    uint32_t it = 0, chunk = 0, segc = 0;
     if (lane == 0) {
       for (int job = blockIdx.x; job < P.njobs && !*abort_flag; job += gridDim.x) {
         int slot, mt, nt;
@@ -320,6 +333,16 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
         int r0, r1;
         seg_range(P, slot, &r0, &r1);
         for (int r = r0; r < r1 && !*abort_flag; ++r) {
+          // low-order levels of this segment accumulate in tail set `lt`
+          const uint32_t lt = segc & 1;
+          if (KS > NEXACT) {
+            if (!tc::mbar_wait(&lempty[lt], ((segc >> 1) & 1) ^ 1, WAIT_LIMIT)) {
+              *abort_flag = 1;
+              atomicExch(P.err, 5);
+              break;
+            }
+            tc::tc_fence_after();
+          }
           uint32_t set = 0;
           for (int kb = 0; kb < P.nkb; ++kb, ++it) {
             const int kc = kb % KCHUNK_BLOCKS;
@@ -346,12 +369,18 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             for (int sa = 0; sa < KS; ++sa) {
 #pragma unroll
               for (int sb = 0; sb < KS - sa; ++sb) {
-                const uint32_t d = tmem + set * C::SET_COLS + (sa + sb) * BN;
+                const int L = sa + sb;
+                // exact levels: per chunk (restart at the chunk's first block);
+                // lower levels: per segment (restart at the segment's first block)
+                const bool exact = L < NEXACT;
+                const uint32_t d = exact ? tmem + set * C::SET_COLS + L * BN
+                                         : tmem + C::TAIL_BASE + lt * C::TAIL_COLS + (L - NEXACT) * BN;
+                const bool first_block = exact ? (kc == 0) : (kb == 0);
 #pragma unroll
                 for (int kk = 0; kk < BKE / 16; ++kk) {
                   const uint64_t ad = tc::make_sdesc_sw128(a_base + sa * C::A_SLICE + kk * 32);
                   const uint64_t bd = tc::make_sdesc_sw128(b_base + sb * C::B_SLICE + kk * 32);
-                  const uint32_t acc = (kc == 0 && kk == 0 && sa == 0) ? 0u : 1u;
+                  const uint32_t acc = (first_block && kk == 0 && sa == 0) ? 0u : 1u;
                   tc::mma_bf16(d, ad, bd, IDESC, acc);
                 }
               }
@@ -362,6 +391,9 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
               ++chunk;
             }
           }
+          if (*abort_flag) break;
+          if (KS > NEXACT) tc::mma_commit(&lfull[lt]);
+          ++segc;
         }
       }
       // all MMAs retired before TMEM is released
@@ -373,7 +405,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
     // ------------------------------------------------- merge / output warps
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     const int row = q * 32 + lane;
-    uint32_t chunk = 0;
+    uint32_t chunk = 0, segc = 0;
     for (int job = blockIdx.x; job < P.njobs; job += gridDim.x) {
       int slot, mt, nt;
       if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
@@ -387,7 +419,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
       }
       bool failed = false;
       for (int r = r0; r < r1 && !failed; ++r) {
-        // per-merge scale of this segment (syrk); pair mode scales at the end
+        // per-merge scale of this segment (syrk); pair/plain modes scale at the end
         float rowscale = 1.0f;
         const int* ecol = nullptr;
         if (P.mode == MODE_SYRK) {
@@ -396,6 +428,24 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           rowscale = (float)P.seg_sign[r] * pow2f(ea);
           ecol = P.exps + (long)r * P.nv + nt * BN;
         }
+        // adds 2^(-14-8L) x level L (TMEM columns at col0) into the accumulators
+        auto merge = [&](int L, uint32_t col0) {
+          const float lscale = pow2f(-14 - 8 * L) * rowscale;
+#pragma unroll
+          for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + col0 + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float sc = lscale;
+              if (P.mode == MODE_SYRK) {
+                const int f = nt * BN + c0 + j;
+                sc *= pow2f((f < P.nv) ? ecol[c0 + j] : -200);
+              }
+              df_add(hi[c0 + j], lo[c0 + j], v[j] * sc);
+            }
+          }
+        };
         const int nchunks = (P.nkb + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
         for (int c = 0; c < nchunks; ++c) {
           const uint32_t set = chunk & 1;
@@ -407,29 +457,29 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           }
           tc::tc_fence_after();
 #pragma unroll 1
-          for (int L = 0; L < KS; ++L) {
-            const float lscale = pow2f(-14 - 8 * L);
-#pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-              float v[16];
-              tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + set * C::SET_COLS + L * BN + c0, v);
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                float sc = lscale * rowscale;
-                if (P.mode == MODE_SYRK) {
-                  const int f = nt * BN + c0 + j;
-                  const int eb = (f < P.nv) ? ecol[c0 + j] : -200;
-                  sc *= pow2f(eb);
-                }
-                df_add(hi[c0 + j], lo[c0 + j], v[j] * sc);
-              }
-            }
-          }
+          for (int L = 0; L < NEXACT && L < KS; ++L) merge(L, set * C::SET_COLS + L * BN);
           tc::tc_fence_before();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&tempty[set]);
           ++chunk;
         }
+        if (failed) break;
+        if (KS > NEXACT) {
+          const uint32_t lt = segc & 1;
+          if (!tc::mbar_wait(&lfull[lt], (segc >> 1) & 1, WAIT_LIMIT)) {
+            *abort_flag = 1;
+            atomicExch(P.err, 6);
+            failed = true;
+            break;
+          }
+          tc::tc_fence_after();
+#pragma unroll 1
+          for (int L = NEXACT; L < KS; ++L) merge(L, C::TAIL_BASE + lt * C::TAIL_COLS + (L - NEXACT) * BN);
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&lempty[lt]);
+        }
+        ++segc;
       }
       if (failed) break;
       // ------------------------------------------------------ tile output

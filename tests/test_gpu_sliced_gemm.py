@@ -73,7 +73,7 @@ def test_sliced_gemm_matches_planed_product(ks):
     ref *= 2.0 ** (ea[:, None] + eb[None, :])
     err = np.abs(C - ref) / (np.abs(ref).max())
     print(ks, "max rel err vs planed product", err.max())
-    assert err.max() < 1e-13
+    assert err.max() < 1e-12   # levels >= 3 are accumulated in float32 (rounded)
     exact = A @ B.T
     rel = np.abs(C - exact).max() / np.abs(exact).max()
     print(ks, "vs float64 product", rel)
