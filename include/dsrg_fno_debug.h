@@ -24,6 +24,17 @@ int dsrg_fno_debug_sliced_gemm(int32_t nslices, int32_t M, int32_t N, int32_t K,
 int dsrg_fno_debug_slice_rows(int32_t nslices, int32_t R, int32_t K, const double* rows, float* planes,
                               int32_t* exps);
 
+/* Digit planes of double-float rows: rows[R][K][2] holds hi, lo float32
+ * pairs (value hi + lo).  Output layout as dsrg_fno_debug_slice_rows. */
+int dsrg_fno_debug_slice_rows_dd(int32_t nslices, int32_t R, int32_t K, const float* rows, float* planes,
+                                 int32_t* exps);
+
+/* The Eq. A7 regulariser as the fast form evaluates it (double-float):
+ * r1[k] = (1 - exp(-s delta[k]^2)) / delta[k] (0 at delta = 0) and
+ * y[k] = exp(-s delta[k]^2), for n host float64 inputs; outputs are host
+ * float64 (the double-float value rounded). */
+int dsrg_fno_debug_regularizer(int32_t n, const double* delta, double s, double* r1, double* y);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,6 +26,8 @@ EXPORTED = (
     "dsrg_fno_release",
     "dsrg_fno_debug_sliced_gemm",
     "dsrg_fno_debug_slice_rows",
+    "dsrg_fno_debug_slice_rows_dd",
+    "dsrg_fno_debug_regularizer",
     "dsrg_fno_profile_enable",
     "dsrg_fno_profile_query",
     "dsrg_fno_launch_count",
@@ -79,6 +81,9 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_debug_sliced_gemm.argtypes = [i32, i32, i32, i32, dp, dp, dp]
     lib.dsrg_fno_debug_slice_rows.argtypes = [i32, i32, i32, dp, ctypes.POINTER(ctypes.c_float),
                                               ctypes.POINTER(i32)]
+    lib.dsrg_fno_debug_slice_rows_dd.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_float),
+                                                 ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
+    lib.dsrg_fno_debug_regularizer.argtypes = [i32, dp, d, dp, dp]
     lib.dsrg_fno_profile_enable.argtypes = [i32]
     lib.dsrg_fno_profile_enable.restype = None
     lib.dsrg_fno_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),

@@ -48,64 +48,69 @@ int ws_reserve(Workspace& ws, size_t bytes) {
 // ---------------------------------------------------------------------------
 struct Batch {
   int pair_begin, npairs, desc_begin, ndesc;
+  int nout;  // dressed matrices written (a core-core pair writes two)
+  int ncc;   // leading work items that are core-core groups
 };
 
 struct Plan {
   std::vector<int2> pairs;
   std::vector<DressDesc> desc;
   std::vector<Batch> batches;
-  int max_pairs = 0, max_desc = 0;
+  int max_pairs = 0, max_desc = 0, max_out = 0;
 };
 
 static void build_plan(int nc, int na, long cap_pairs, Plan& P) {
   struct Group {
     std::vector<int2> pairs;
-    std::vector<DressDesc> desc;  // slot/out relative to the group
+    int kind, nout;
   };
   std::vector<Group> groups;
   for (int m = 0; m < nc; ++m)
     for (int n = m; n < nc; ++n) {
       Group G;
       G.pairs.push_back(make_int2(m, n));
-      if (m == n) G.desc.push_back({DRESS_CC_DIAG, 0, 0, 0, 0});
-      else {
-        G.desc.push_back({DRESS_CC_SYM, 0, 0, 0, 0});
-        G.desc.push_back({DRESS_CC_ANTI, 0, 0, 0, 0});
-      }
+      G.kind = (m == n) ? GROUP_CC_DIAG : GROUP_CC_PAIR;
+      G.nout = (m == n) ? 1 : 2;
       groups.push_back(G);
     }
   if (na > 0) {
     for (int m = 0; m < nc; ++m) {
       Group G;
       for (int u = 0; u < na; ++u) G.pairs.push_back(make_int2(m, nc + u));
-      for (int k = 0; k < na; ++k) {
-        G.desc.push_back({DRESS_CA_SYM, 0, k, m, 0});
-        G.desc.push_back({DRESS_CA_ANTI, 0, k, m, 0});
-      }
+      G.kind = GROUP_CA;
+      G.nout = 2 * na;
       groups.push_back(G);
     }
     Group G;
     for (int u = 0; u < na; ++u)
       for (int v = u; v < na; ++v) G.pairs.push_back(make_int2(nc + u, nc + v));
-    const int ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
-    for (int k = 0; k < ns; ++k) G.desc.push_back({DRESS_AA_SYM, 0, k, 0, 0});
-    for (int k = 0; k < nd; ++k) G.desc.push_back({DRESS_AA_ANTI, 0, k, 0, 0});
+    G.kind = GROUP_AA;
+    G.nout = na * na;  // na (na + 1) / 2 symmetric + na (na - 1) / 2 antisymmetric
     groups.push_back(G);
   }
   long largest = 0;
   for (auto& G : groups) largest = std::max<long>(largest, (long)G.pairs.size());
   cap_pairs = std::max(cap_pairs, largest);
-  Batch cur{0, 0, 0, 0};
+  Batch cur{0, 0, 0, 0, 0, 0};
   for (auto& G : groups) {
     if (cur.npairs > 0 && cur.npairs + (long)G.pairs.size() > cap_pairs) {
       P.batches.push_back(cur);
-      cur = Batch{(int)P.pairs.size(), 0, (int)P.desc.size(), 0};
+      cur = Batch{(int)P.pairs.size(), 0, (int)P.desc.size(), 0, 0, 0};
     }
-    for (auto d : G.desc) {
-      d.slot += cur.npairs;
-      d.out = cur.ndesc++;
+    for (int o0 = 0; o0 < G.nout; o0 += DRESS_OC) {
+      DressDesc d{};
+      d.kind = G.kind;
+      d.slot = cur.npairs;
+      d.nslots = (int)G.pairs.size();
+      d.out = cur.nout;
+      d.o_begin = o0;
+      d.o_count = std::min(DRESS_OC, G.nout - o0);
+      d.m = G.pairs[0].x;
       P.desc.push_back(d);
+      ++cur.ndesc;
+      if (G.kind == GROUP_CC_DIAG || G.kind == GROUP_CC_PAIR) ++cur.ncc;
     }
+    cur.nout += G.nout;
     for (auto p : G.pairs) P.pairs.push_back(p);
     cur.npairs += (int)G.pairs.size();
   }
@@ -113,6 +118,7 @@ static void build_plan(int nc, int na, long cap_pairs, Plan& P) {
   for (auto& b : P.batches) {
     P.max_pairs = std::max(P.max_pairs, b.npairs);
     P.max_desc = std::max(P.max_desc, b.ndesc);
+    P.max_out = std::max(P.max_out, b.nout);
   }
 }
 
@@ -184,8 +190,13 @@ struct PassBuffers {
   int kpad_q, kpad_v; // padded contraction lengths (naux, nvir)
   __nv_bfloat16 *planes_b, *planes_s;
   int *exps_b, *exps_s, *err;
-  double* nu;
+  float2* nu;      // double-float contraction tiles
+  float2* eps_dd;  // orbital energies as double-float
 };
+
+// In the fast form tau, kappa and the dressed matrices are double-float
+// (float2, the same 8 bytes per element as the float64 form's buffers).
+static float2* as_dd(double* p) { return reinterpret_cast<float2*>(p); }
 
 static const int DEFAULT_SLICES = 5;
 
@@ -240,6 +251,7 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
     const long rows = (long)g.nh * g.np;
     DSRG_PHASE("phase_stage_b", st);
     DSRG_TRY(slice_rows(W.ks, B, rows, g.nq, 1, rows, W.kpad_q, W.planes_b, W.exps_b, st));
+    DSRG_TRY(eps_to_dd(g.nh + g.nv, eps, W.eps_dd, st));
   }
   for (size_t bi = 0; bi < P.batches.size(); ++bi) {
     const Batch& b = P.batches[bi];
@@ -248,25 +260,32 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
       DSRG_TRY(sliced_pair_gemm(W.ks, g, W.planes_b, W.exps_b, W.kpad_q, W.pairs + b.pair_begin, b.npairs,
                                 ts == nullptr, W.nu, W.err, st));
       DSRG_PHASE("phase_pair_epilogue", st);
-      DSRG_TRY(pair_epilogue(g, eps, W.pairs + b.pair_begin, b.npairs, W.nu, W.tau, W.kap, ts, st));
+      DSRG_TRY(pair_epilogue_dd(g, eps, W.eps_dd, W.pairs + b.pair_begin, b.npairs, W.nu, as_dd(W.tau),
+                                as_dd(W.kap), ts, st));
     } else {
       DSRG_TRY(pair_gemm_f64(g, B, eps, W.pairs + b.pair_begin, b.npairs, W.tau, W.kap, ts, st));
     }
     {
       DSRG_PHASE("phase_dress", st);
-      DSRG_TRY(dress_f64(g, W.desc + b.desc_begin, b.ndesc, aux, W.tau, W.kap, W.sig, W.sig_sign, W.e_part,
-                         want_d, st));
+      if (W.ks)
+        DSRG_TRY(dress_dd(g, W.desc + b.desc_begin, b.ndesc, b.ncc, aux, as_dd(W.tau), as_dd(W.kap), as_dd(W.sig),
+                          W.sig_sign, W.e_part, want_d, st));
+      else
+        DSRG_TRY(dress_f64(g, W.desc + b.desc_begin, b.ndesc, b.ncc, aux, W.tau, W.kap, W.sig, W.sig_sign,
+                           W.e_part, want_d, st));
     }
-    DSRG_TRY(ordered_sum(W.e_part, (long)b.ndesc * ntd * ntd, W.e_acc, bi > 0, st));
+    DSRG_TRY(ordered_sum(W.e_part, (long)b.ndesc * DRESS_TILE_BLOCKS, W.e_acc, bi > 0, st));
     if (want_d) {
       if (W.ks) {
-        const long rows = (long)b.ndesc * g.nv;
-        DSRG_PHASE("phase_stage_sig", st);
-        DSRG_TRY(slice_rows(W.ks, W.sig, rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, st));
-        DSRG_TRY(sliced_syrk(W.ks, g.nv, b.ndesc, W.planes_s, W.exps_s, W.kpad_v, W.sig_sign, W.dpart, W.nsplit, D,
+        const long rows = (long)b.nout * g.nv;
+        {
+          DSRG_PHASE("phase_stage_sig", st);
+          DSRG_TRY(slice_rows_dd(W.ks, as_dd(W.sig), rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, st));
+        }
+        DSRG_TRY(sliced_syrk(W.ks, g.nv, b.nout, W.planes_s, W.exps_s, W.kpad_v, W.sig_sign, W.dpart, W.nsplit, D,
                              W.err, st));
       } else {
-        DSRG_TRY(syrk_dressed_f64(g.nv, b.ndesc, W.sig, W.sig_sign, W.dpart, W.nsplit, D, st));
+        DSRG_TRY(syrk_dressed_f64(g.nv, b.nout, W.sig, W.sig_sign, W.dpart, W.nsplit, D, st));
       }
     }
   }
@@ -291,9 +310,9 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
   b += ws_bytes(P.pairs.size(), sizeof(int2));
   b += ws_bytes(P.desc.size(), sizeof(DressDesc));
   b += 2 * doubles((size_t)P.max_pairs * nv2);
-  b += doubles(want_d ? (size_t)P.max_desc * nv2 : 1);
-  b += doubles((size_t)P.max_desc + 1);
-  b += doubles((size_t)P.max_desc * ntd * ntd + 1);
+  b += doubles(want_d ? (size_t)P.max_out * nv2 : 1);
+  b += doubles((size_t)P.max_out + 1);
+  b += doubles((size_t)P.max_desc * DRESS_TILE_BLOCKS + 1);
   b += doubles(want_d ? (size_t)nsplit * nv2 : 1);
   b += doubles(want_d && na ? (size_t)g.nh * g.nh * g.nv * na : 1);
   b += doubles(8);
@@ -305,8 +324,9 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
     const size_t rows = (size_t)g.nh * g.np;
     b += ws_bytes((size_t)ks * rows * pad64(g.nq), 2) + ws_bytes(rows, sizeof(int));
     b += doubles((size_t)P.max_pairs * g.np * g.np);
+    b += doubles((size_t)g.nh + g.nv);
     if (want_d)
-      b += ws_bytes((size_t)ks * P.max_desc * g.nv * pad64(g.nv), 2) + ws_bytes((size_t)P.max_desc * g.nv, sizeof(int));
+      b += ws_bytes((size_t)ks * P.max_out * g.nv * pad64(g.nv), 2) + ws_bytes((size_t)P.max_out * g.nv, sizeof(int));
     b += ws_bytes(8, sizeof(int));
   }
   return b;
@@ -321,9 +341,9 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
   W.desc = ws_take<DressDesc>(ws, P.desc.size());
   W.tau = ws_take<double>(ws, (size_t)P.max_pairs * nv2);
   W.kap = ws_take<double>(ws, (size_t)P.max_pairs * nv2);
-  W.sig = ws_take<double>(ws, want_d ? (size_t)P.max_desc * nv2 : 1);
-  W.sig_sign = ws_take<double>(ws, (size_t)P.max_desc + 1);
-  W.e_part = ws_take<double>(ws, (size_t)P.max_desc * ntd * ntd + 1);
+  W.sig = ws_take<double>(ws, want_d ? (size_t)P.max_out * nv2 : 1);
+  W.sig_sign = ws_take<double>(ws, (size_t)P.max_out + 1);
+  W.e_part = ws_take<double>(ws, (size_t)P.max_desc * DRESS_TILE_BLOCKS + 1);
   W.dpart = ws_take<double>(ws, want_d ? (size_t)nsplit * nv2 : 1);
   W.ts = ws_take<double>(ws, want_d && na ? (size_t)g.nh * g.nh * g.nv * na : 1);
   W.e_acc = ws_take<double>(ws, 8);
@@ -347,10 +367,11 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
     W.kpad_v = pad64(g.nv);
     W.planes_b = ws_take<__nv_bfloat16>(ws, (size_t)ks * rows * W.kpad_q);
     W.exps_b = ws_take<int>(ws, rows);
-    W.nu = ws_take<double>(ws, (size_t)P.max_pairs * g.np * g.np);
+    W.nu = ws_take<float2>(ws, (size_t)P.max_pairs * g.np * g.np);
+    W.eps_dd = ws_take<float2>(ws, (size_t)g.nh + g.nv);
     if (want_d) {
-      W.planes_s = ws_take<__nv_bfloat16>(ws, (size_t)ks * P.max_desc * g.nv * W.kpad_v);
-      W.exps_s = ws_take<int>(ws, (size_t)P.max_desc * g.nv);
+      W.planes_s = ws_take<__nv_bfloat16>(ws, (size_t)ks * P.max_out * g.nv * W.kpad_v);
+      W.exps_s = ws_take<int>(ws, (size_t)P.max_out * g.nv);
     }
     W.err = ws_take<int>(ws, 8);
     if (!W.err) return DSRG_FNO_ERR_NOMEM;
@@ -471,7 +492,7 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   const int ks = slices_of(prob);
   Plan P;
   build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, device_budget() + ws.cap / 2), P);
-  const int nsplit = nsplit_for(g.nv, P.max_desc);
+  const int nsplit = nsplit_for(g.nv, P.max_out);
   const size_t small = small_terms_work_doubles(g.nc, g.na, g.nv);
   const int kmax = small_terms_kmax(g.nc, g.na);
   const bool small_fast = ks > 0 && kmax >= SLICED_MIN_K;

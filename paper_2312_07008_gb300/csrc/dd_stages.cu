@@ -1,0 +1,306 @@
+// Elementwise stages of the fast form in double-float arithmetic:
+//   - the Eq. A7 regulariser applied to the contraction tiles (tau, kappa),
+//   - the 2-RDM dressing of the vv classes with the energy partials.
+// Their float64 counterparts are gemm_f64.cu (fused epilogue) and dress.cu.
+//
+// Regulariser.  With x = s Delta^2 >= 0, y = exp(-x):
+//   tau = nu (1 - y) / Delta,  kappa = 2 nu - Delta tau = nu (1 + y).
+// exp(-x) follows the table method of Tang (ACM TOMS 15, 1989): t = x log2(e)
+// = n/64 + r with |r| <= 1/128, u = r ln 2, exp(-x) = 2^-q 2^-j/64 exp(-u),
+// n = 64 q + j, and exp(-u) from its Taylor series (to the cubic term in
+// double-float).  1 - y is formed without
+// cancellation: with C_j = 1 - 2^-j/64 and 1 - exp(-u) = u - u^2/2 + ...,
+//   1 - y = C_j + (1 - e^-u) - C_j (1 - e^-u)     (q = 0),
+// so that the small-Delta branch of Eq. A7 (R -> s Delta) keeps its relative
+// accuracy without a separate series.  For x > 40, y < 5e-18 is dropped.
+#include "dd.cuh"
+#include "dress_common.cuh"
+#include "kernels.h"
+
+namespace dsrg {
+
+namespace {
+
+using namespace dressc;
+
+struct RegTables {
+  dd T[64];  // 2^-j/64
+  dd C[64];  // 1 - 2^-j/64
+  dd log2e, ln2, sixth;
+};
+
+__device__ void reg_tables_init(RegTables& R) {
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    R.T[j] = dd_from_double(exp2(-j / 64.0));
+    R.C[j] = dd_from_double(-expm1(-j * 0.69314718055994530942 / 64.0));
+  }
+  if (threadIdx.x == 0) {
+    R.log2e = dd_from_double(1.44269504088896340736);
+    R.ln2 = dd_from_double(0.69314718055994530942);
+    R.sixth = dd_from_double(1.0 / 6.0);
+  }
+}
+
+// R1 = (1 - exp(-s Delta^2)) / Delta and y = exp(-s Delta^2), double-float.
+__device__ __forceinline__ void regularize(dd delta, dd s, const RegTables& R, dd* r1, dd* y) {
+  if (delta.hi == 0.0f) {
+    *r1 = dd_make(0.0f);
+    *y = dd_make(1.0f);
+    return;
+  }
+  const dd x = dd_mul(s, dd_mul(delta, delta));
+  if (x.hi < 1e-20f) {  // R1 = s Delta (1 - x/2 + ...), y = 1 - x: the x terms are below the precision
+    *r1 = dd_mul(s, delta);
+    *y = dd_make(1.0f);
+    return;
+  }
+  if (x.hi > 40.0f) {
+    *y = dd_make(0.0f);
+    *r1 = dd_div(dd_make(1.0f), delta);
+    return;
+  }
+  const dd t = dd_mul(x, R.log2e);
+  const int n = __float2int_rn(t.hi * 64.0f);
+  const dd r = dd_sub(t, dd_make((float)n * 0.015625f));
+  const dd u = dd_mul(r, R.ln2);
+  const float uh = u.hi;
+  // 1 - e^-u = u - u^2/2 + u^3/6 - (u^4/24 - u^5/120 + u^6/720)   (|u| <= 0.0055)
+  // up to the cubic term in double-float; the rest (< 4e-11) in float
+  const dd u2 = dd_mul(u, u);
+  const dd c3 = dd_mul(dd_mul(u2, u), R.sixth);
+  const float tail = uh * uh * uh * uh * (1.0f / 24.0f - uh * (1.0f / 120.0f - uh * (1.0f / 720.0f)));
+  const dd omp = dd_add_f(dd_add(dd_sub(u, dd_mul_f(u2, 0.5f)), c3), -tail);
+  const dd p = dd_sub(dd_make(1.0f), omp);
+  const int q = n >> 6, j = n & 63;
+  *y = dd_ldexp(dd_mul(R.T[j], p), -q);
+  dd omy;
+  if (q == 0) omy = dd_add(R.C[j], dd_sub(omp, dd_mul(R.C[j], omp)));
+  else omy = dd_sub(dd_make(1.0f), *y);
+  *r1 = dd_div(omy, delta);
+}
+
+// tau / kappa (vv, double-float) and t^{ij}_{ex} (va / av, float64) from the
+// double-float contraction tiles nu[slot][a][b].  One block per (row a, slot).
+__global__ void eps_dd_kernel(int n, const double* __restrict__ eps, float2* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    const dd v = dd_from_double(eps[k]);
+    out[k] = make_float2(v.hi, v.lo);
+  }
+}
+
+__global__ void __launch_bounds__(256) pair_epilogue_dd_kernel(Geometry g, const double* __restrict__ eps,
+                                                               const float2* __restrict__ eps_dd,
+                                                               const int2* __restrict__ pairs,
+                                                               const float2* __restrict__ nu,
+                                                               float2* __restrict__ tau, float2* __restrict__ kap,
+                                                               double* __restrict__ ts) {
+  __shared__ RegTables R;
+  reg_tables_init(R);
+  __syncthreads();
+  const int a = blockIdx.x, slot = blockIdx.y;
+  const int na = g.na, nv = g.nv, np = g.np;
+  const bool av = a >= na;
+  const int2 pr = pairs[slot];
+  const int i = pr.x, j = pr.y;
+  const double* ep = eps + g.nc;
+  // Delta = (eps_i + eps_j - eps_a) - eps_b, rounded once to double-float per row
+  const dd ca = dd_from_double(eps[i] + eps[j] - ep[a]);
+  const dd s = dd_from_double(g.s);
+  const float2* nrow = nu + ((long)slot * np + a) * np;
+  for (int b = threadIdx.x; b < np; b += blockDim.x) {
+    const bool bv = b >= na;
+    if (!av && !bv) continue;
+    if (ts == nullptr && !(av && bv)) continue;
+    const float2 nn = nrow[b];
+    const dd n = {nn.x, nn.y};
+    const float2 eb = eps_dd[g.nc + b];
+    const dd delta = dd_sub(ca, dd{eb.x, eb.y});
+    dd r1, y;
+    regularize(delta, s, R, &r1, &y);
+    const dd t = dd_mul(n, r1);
+    if (av && bv) {
+      const dd k = dd_mul(n, dd_add_f(y, 1.0f));
+      const long o = ((long)slot * nv + (a - na)) * nv + (b - na);
+      tau[o] = make_float2(t.hi, t.lo);
+      kap[o] = make_float2(k.hi, k.lo);
+    } else if (av) {
+      ts[(((long)i * g.nh + j) * nv + (a - na)) * na + b] = dd_to_double(t);
+    } else if (i != j) {
+      ts[(((long)j * g.nh + i) * nv + (b - na)) * na + a] = dd_to_double(t);
+    }
+  }
+}
+
+__device__ __forceinline__ dd ld(const float2* p, long i) {
+  const float2 v = p[i];
+  return {v.x, v.y};
+}
+
+// Double-float form of the group dressing (same structure as dress.cu).
+template <int OCT>
+__global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const DressDesc* __restrict__ desc,
+                                                       DressAux aux, const float2* __restrict__ tau,
+                                                       const float2* __restrict__ kap, float2* __restrict__ sig,
+                                                       double* __restrict__ sig_sign, double* __restrict__ e_part,
+                                                       int want_sig) {
+  constexpr int NS = (OCT == 2) ? 1 : MAXSLOT;
+  // float64 coefficients, converted in place to double-float (same size)
+  __shared__ union {
+    double d[NS][OCT];
+    dd f[NS][OCT];
+  } cf;
+  __shared__ double lam[OCT], sgn[OCT], dg[NS];
+  __shared__ dd lamw[OCT], sqd[OCT];
+  __shared__ float2 tT[GT][GT + 1], tK[GT][GT + 1], sA[GT][GT + 1];
+  __shared__ double red[GNT / 32];
+  const DressDesc D = desc[blockIdx.y];
+  group_coefficients<OCT>(D, aux, na, cf.d, lam, sgn, dg);
+  const int oc = D.o_count;
+  for (int idx = threadIdx.x; idx < D.nslots * OCT; idx += blockDim.x) {
+    const int u = idx / OCT, o = idx % OCT;
+    const double v = cf.d[u][o];
+    cf.f[u][o] = dd_from_double(v);
+  }
+  for (int o = threadIdx.x; o < oc; o += blockDim.x) {
+    lamw[o] = dd_from_double(0.5 * lam[o]);
+    sqd[o] = dd_from_double(sqrt(fabs(lam[o])));
+  }
+  __syncthreads();
+  const int ntd = (nv + GT - 1) / GT;
+  const int nup = ntd * (ntd + 1) / 2;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const long nv2 = (long)nv * nv;
+  dd part = dd_make(0.0f);
+  for (int t = blockIdx.x; t < nup; t += gridDim.x) {
+    int rem = t, te = 0;
+    while (rem >= ntd - te) {
+      rem -= ntd - te;
+      ++te;
+    }
+    const int tf = te + rem;
+    const int E0 = te * GT, F0 = tf * GT;
+    const int e = E0 + ty, f = F0 + tx;
+    const bool inside = e < nv && f < nv;
+    const float w = (te == tf) ? 1.0f : 2.0f;
+    dd at[OCT], ak[OCT];
+#pragma unroll
+    for (int o = 0; o < OCT; ++o) {
+      at[o] = dd_make(0.0f);
+      ak[o] = dd_make(0.0f);
+    }
+    for (int u = 0; u < D.nslots; ++u) {
+      const float2* T = tau + (long)(D.slot + u) * nv2;
+      const float2* K = kap + (long)(D.slot + u) * nv2;
+      {
+        const int fr = F0 + ty, ec = E0 + tx;
+        const bool ok = fr < nv && ec < nv;
+        tT[ty][tx] = ok ? T[(long)fr * nv + ec] : make_float2(0.f, 0.f);
+        tK[ty][tx] = ok ? K[(long)fr * nv + ec] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      const dd a = inside ? ld(T, (long)e * nv + f) : dd_make(0.0f);
+      const dd b = inside ? ld(K, (long)e * nv + f) : dd_make(0.0f);
+      const dd att = {tT[tx][ty].x, tT[tx][ty].y}, btt = {tK[tx][ty].x, tK[tx][ty].y};
+#pragma unroll
+      for (int o = 0; o < OCT; ++o) {
+        if (o < oc) {
+          const dd c = cf.f[u][o];
+          const float m2 = (float)(sgn[o] * dg[u]);  // +1, -1 or 0
+          const dd c2 = {c.hi * m2, c.lo * m2};
+          at[o] = dd_add(at[o], dd_add(dd_mul(c, a), dd_mul(c2, att)));
+          ak[o] = dd_add(ak[o], dd_add(dd_mul(c, b), dd_mul(c2, btt)));
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int o = 0; o < OCT; ++o) {
+      if (o < oc) {
+        if (inside) part = dd_add(part, dd_mul_f(dd_mul(lamw[o], dd_mul(at[o], ak[o])), w));
+        if (want_sig) {
+          const dd v = dd_mul(sqd[o], at[o]);
+          float2* S = sig + (long)(D.out + D.o_begin + o) * nv2;
+          if (inside) S[(long)e * nv + f] = make_float2(v.hi, v.lo);
+          if (te != tf) {
+            sA[ty][tx] = make_float2(v.hi, v.lo);
+            __syncthreads();
+            const int fr = F0 + ty, ec = E0 + tx;
+            const float sg = (float)sgn[o];
+            if (fr < nv && ec < nv) S[(long)fr * nv + ec] = make_float2(sg * sA[tx][ty].x, sg * sA[tx][ty].y);
+            __syncthreads();
+          }
+        }
+      }
+    }
+  }
+  double pd = dd_to_double(part);
+  for (int o = 16; o > 0; o >>= 1) pd += __shfl_down_sync(0xffffffffu, pd, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pd;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int wv = 0; wv < GNT / 32; ++wv) s += red[wv];
+    e_part[(long)blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+  if (want_sig && blockIdx.x == 0 && threadIdx.x < oc)
+    sig_sign[D.out + D.o_begin + threadIdx.x] = (lam[threadIdx.x] >= 0.0) ? 1.0 : -1.0;
+}
+
+// n regulariser values for tests: r1[k] = R1(delta[k]), y[k] = exp(-s delta^2)
+__global__ void regularize_test_kernel(int n, const double* delta, double s, double* r1, double* y) {
+  __shared__ RegTables R;
+  reg_tables_init(R);
+  __syncthreads();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    dd a, b;
+    regularize(dd_from_double(delta[k]), dd_from_double(s), R, &a, &b);
+    r1[k] = dd_to_double(a);
+    y[k] = dd_to_double(b);
+  }
+}
+
+}  // namespace
+
+int eps_to_dd(int n, const double* eps, float2* out, cudaStream_t st) {
+  if (n <= 0) return DSRG_FNO_OK;
+  eps_dd_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, eps, out);
+  DSRG_LAUNCH_CHECK();
+  return DSRG_FNO_OK;
+}
+
+int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd, const int2* pairs, int npairs,
+                     const float2* nu, float2* tau, float2* kap, double* ts, cudaStream_t st) {
+  if (npairs <= 0) return DSRG_FNO_OK;
+  dim3 grid(g.np, npairs);
+  pair_epilogue_dd_kernel<<<grid, 256, 0, st>>>(g, eps, eps_dd, pairs, nu, tau, kap, ts);
+  DSRG_LAUNCH_CHECK();
+  return DSRG_FNO_OK;
+}
+
+int dress_dd(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, const DressAux& aux,
+             const float2* tau, const float2* kap, float2* sig, double* sig_sign, double* e_part, bool want_sig,
+             cudaStream_t st) {
+  if (ncc > 0) {
+    dim3 grid(DRESS_TILE_BLOCKS, ncc);
+    dress_dd_kernel<2><<<grid, GNT, 0, st>>>(g.nv, g.na, d_desc, aux, tau, kap, sig, sig_sign, e_part,
+                                             want_sig ? 1 : 0);
+    DSRG_LAUNCH_CHECK();
+  }
+  if (ndesc > ncc) {
+    dim3 grid(DRESS_TILE_BLOCKS, ndesc - ncc);
+    dress_dd_kernel<DRESS_OC><<<grid, GNT, 0, st>>>(g.nv, g.na, d_desc + ncc, aux, tau, kap, sig, sig_sign,
+                                                    e_part + (long)ncc * DRESS_TILE_BLOCKS, want_sig ? 1 : 0);
+    DSRG_LAUNCH_CHECK();
+  }
+  return DSRG_FNO_OK;
+}
+
+int regularize_test(int n, const double* delta, double s, double* r1, double* y, cudaStream_t st) {
+  if (n <= 0) return DSRG_FNO_OK;
+  regularize_test_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, delta, s, r1, y);
+  DSRG_LAUNCH_CHECK();
+  return DSRG_FNO_OK;
+}
+
+}  // namespace dsrg

@@ -62,3 +62,35 @@ extern "C" int dsrg_fno_debug_slice_rows(int32_t ks, int32_t R, int32_t K, const
   DSRG_CUDA(cudaMemcpy(exps, e.p, sizeof(int) * R, cudaMemcpyDeviceToHost));
   return DSRG_FNO_OK;
 }
+
+extern "C" int dsrg_fno_debug_slice_rows_dd(int32_t ks, int32_t R, int32_t K, const float* rows, float* planes,
+                                            int32_t* exps) {
+  if (ks < 3 || ks > 5 || R <= 0 || K <= 0 || !rows || !planes || !exps) return DSRG_FNO_ERR_ARG;
+  const int kp = pad64(K);
+  DevBuf d, p, e;
+  DSRG_CUDA(cudaMalloc(&d.p, sizeof(float2) * R * K));
+  DSRG_CUDA(cudaMalloc(&p.p, 2L * ks * R * kp));
+  DSRG_CUDA(cudaMalloc(&e.p, sizeof(int) * R));
+  DSRG_CUDA(cudaMemcpy(d.p, rows, sizeof(float2) * R * K, cudaMemcpyHostToDevice));
+  DSRG_TRY(slice_rows_dd(ks, (float2*)d.p, R, K, K, 1, kp, (__nv_bfloat16*)p.p, (int*)e.p, 0));
+  DSRG_CUDA(cudaDeviceSynchronize());
+  std::vector<__nv_bfloat16> h((size_t)ks * R * kp);
+  DSRG_CUDA(cudaMemcpy(h.data(), p.p, h.size() * 2, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < h.size(); ++i) planes[i] = __bfloat162float(h[i]);
+  DSRG_CUDA(cudaMemcpy(exps, e.p, sizeof(int) * R, cudaMemcpyDeviceToHost));
+  return DSRG_FNO_OK;
+}
+
+extern "C" int dsrg_fno_debug_regularizer(int32_t n, const double* delta, double s, double* r1, double* y) {
+  if (n <= 0 || !delta || !r1 || !y || !(s >= 0.0)) return DSRG_FNO_ERR_ARG;
+  DevBuf d, a, b;
+  DSRG_CUDA(cudaMalloc(&d.p, sizeof(double) * n));
+  DSRG_CUDA(cudaMalloc(&a.p, sizeof(double) * n));
+  DSRG_CUDA(cudaMalloc(&b.p, sizeof(double) * n));
+  DSRG_CUDA(cudaMemcpy(d.p, delta, sizeof(double) * n, cudaMemcpyHostToDevice));
+  DSRG_TRY(regularize_test(n, (double*)d.p, s, (double*)a.p, (double*)b.p, 0));
+  DSRG_CUDA(cudaDeviceSynchronize());
+  DSRG_CUDA(cudaMemcpy(r1, a.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  DSRG_CUDA(cudaMemcpy(y, b.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  return DSRG_FNO_OK;
+}

@@ -13,184 +13,114 @@
 // and the group contributes
 //   D += sum_r lambda_r sigma_r sigma_r^T,   E += 1/2 sum_r lambda_r <sigma_r[tau], sigma_r[kappa]>.
 // Core-core:   G = [[4,-2],[-2,4]]  -> lambda 2 (sym), 6 (antisym); diagonal pair 2.
+// (A work item forms up to DRESS_OC outputs of one group in one pass.)
 // Core-active: G = [[2,-1],[-1,2]] (x) Gamma1 -> lambda g_k (sym), 3 g_k (antisym).
 // Active:      eigen-decomposition of the aa block of G (computed on device).
 #include "kernels.h"
+#include "dress_common.cuh"
 
 namespace dsrg {
 
 namespace {
+using namespace dressc;
 
-constexpr int DT = 32;         // tile edge
-constexpr int DNT = 256;       // threads (32 x 8)
-constexpr int MAXENT = 136;    // entries of one dressed matrix (nact <= 16)
-constexpr double RSQ2 = 0.70710678118654752440;
-
-struct Ent {
-  int slot;
-  double cd, ct;  // coefficient of tau^{slot} and of its transpose
-};
-
-__device__ int aa_pair_offset(int u, int v, int na) {
-  // offset of unordered pair (u <= v) in the row-major enumeration u<=v
-  return u * na - u * (u - 1) / 2 + (v - u);
-}
-
-// decode the d-th strictly-upper pair (u < v)
-__device__ void aa_anti_pair(int d, int na, int* uo, int* vo) {
-  int u = 0;
-  while (d >= na - 1 - u) {
-    d -= na - 1 - u;
-    ++u;
-  }
-  *uo = u;
-  *vo = u + 1 + d;
-}
-
-__device__ void build_entries(const DressDesc& D, const DressAux& X, int na, Ent* ent, int* nent,
-                              double* lam) {
-  const int t = threadIdx.x;
-  switch (D.kind) {
-    case DRESS_CC_DIAG:
-      if (t == 0) {
-        ent[0] = {D.slot, 1.0, 0.0};
-        *nent = 1;
-        *lam = 2.0;
-      }
-      break;
-    case DRESS_CC_SYM:
-    case DRESS_CC_ANTI:
-      if (t == 0) {
-        ent[0] = {D.slot, RSQ2, D.kind == DRESS_CC_SYM ? RSQ2 : -RSQ2};
-        *nent = 1;
-        *lam = D.kind == DRESS_CC_SYM ? 2.0 : 6.0;
-      }
-      break;
-    case DRESS_CA_SYM:
-    case DRESS_CA_ANTI: {
-      const int k = D.a;
-      if (t < na) {
-        double w = X.g1_evec[t * na + k] * RSQ2;
-        ent[t] = {D.slot + t, w, D.kind == DRESS_CA_SYM ? w : -w};
-      }
-      if (t == 0) {
-        *nent = na;
-        double g = X.g1_eval[k * (na + 1)];
-        *lam = D.kind == DRESS_CA_SYM ? g : 3.0 * g;
-      }
-      break;
-    }
-    case DRESS_AA_SYM: {
-      const int ns = na * (na + 1) / 2, k = D.a;
-      for (int s = t; s < ns; s += blockDim.x) {
-        // s enumerates (u <= v) in the same order as the aa slots
-        int u = 0, rem = s;
-        while (rem >= na - u) {
-          rem -= na - u;
-          ++u;
-        }
-        int v = u + rem;
-        double y = X.aas_evec[s * ns + k];
-        if (u == v) ent[s] = {D.slot + s, y, 0.0};
-        else ent[s] = {D.slot + s, y * RSQ2, y * RSQ2};
-      }
-      if (t == 0) {
-        *nent = ns;
-        *lam = X.aas_eval[k * (ns + 1)];
-      }
-      break;
-    }
-    case DRESS_AA_ANTI: {
-      const int nd = na * (na - 1) / 2, k = D.a;
-      for (int d = t; d < nd; d += blockDim.x) {
-        int u, v;
-        aa_anti_pair(d, na, &u, &v);
-        double y = X.aaa_evec[d * nd + k] * RSQ2;
-        ent[d] = {D.slot + aa_pair_offset(u, v, na), y, -y};
-      }
-      if (t == 0) {
-        *nent = nd;
-        *lam = X.aaa_eval[k * (nd + 1)];
-      }
-      break;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(DNT) dress_kernel(int nv, int na, const DressDesc* __restrict__ desc,
+// One pass over the upper tiles of a group: every slot tile is read once and
+// all outputs of the work item are formed in registers.  Dressed matrices are
+// symmetric or antisymmetric, so the (F, E) tile of Sig is the signed
+// transpose of the (E, F) tile; the energy of an off-diagonal tile counts
+// twice.
+template <int OCT>
+__global__ void __launch_bounds__(GNT) dress_kernel(int nv, int na, const DressDesc* __restrict__ desc,
                                                     DressAux aux, const double* __restrict__ tau,
                                                     const double* __restrict__ kap,
                                                     double* __restrict__ sig, double* __restrict__ sig_sign,
                                                     double* __restrict__ e_part, int want_sig) {
-  __shared__ Ent ent[MAXENT];
-  __shared__ int nent;
-  __shared__ double lam;
-  __shared__ double tT[DT][DT + 1], tK[DT][DT + 1];
-  __shared__ double red[DNT / 32];
+  constexpr int NS = (OCT == 2) ? 1 : MAXSLOT;  // core-core groups have one slot
+  __shared__ double cd[NS][OCT];
+  __shared__ double lam[OCT], sgn[OCT], dg[NS];
+  __shared__ double tT[GT][GT + 1], tK[GT][GT + 1], sA[GT][GT + 1];
+  __shared__ double red[GNT / 32];
   const DressDesc D = desc[blockIdx.y];
-  build_entries(D, aux, na, ent, &nent, &lam);
-  __syncthreads();
-  const int ntd = (nv + DT - 1) / DT;
-  const int E0 = (blockIdx.x / ntd) * DT, F0 = (blockIdx.x % ntd) * DT;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  group_coefficients<OCT>(D, aux, na, cd, lam, sgn, dg);
+  const int oc = D.o_count;
+  const int ntd = (nv + GT - 1) / GT;
+  const int nup = ntd * (ntd + 1) / 2;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const long nv2 = (long)nv * nv;
-  double st[4] = {0, 0, 0, 0}, sk[4] = {0, 0, 0, 0};
-  for (int q = 0; q < nent; ++q) {
-    const Ent en = ent[q];
-    const double* T = tau + (long)en.slot * nv2;
-    const double* K = kap + (long)en.slot * nv2;
-    // transposed tile: tT[fl][el] = T[F0+fl][E0+el]
-    if (en.ct != 0.0) {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        int fl = ty + 8 * r, f = F0 + fl, e = E0 + tx;
-        double a = 0.0, b = 0.0;
-        if (f < nv && e < nv) {
-          a = T[(long)f * nv + e];
-          b = K[(long)f * nv + e];
-        }
-        tT[fl][tx] = a;
-        tK[fl][tx] = b;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      int el = ty + 8 * r, e = E0 + el, f = F0 + tx;
-      if (e < nv && f < nv) {
-        double a = en.cd * T[(long)e * nv + f];
-        double b = en.cd * K[(long)e * nv + f];
-        if (en.ct != 0.0) {
-          a = fma(en.ct, tT[tx][el], a);
-          b = fma(en.ct, tK[tx][el], b);
-        }
-        st[r] += a;
-        sk[r] += b;
-      }
-    }
-    __syncthreads();
-  }
-  const double l = lam;
-  const double sq = sqrt(fabs(l));
   double part = 0.0;
+  for (int t = blockIdx.x; t < nup; t += gridDim.x) {
+    int rem = t, te = 0;
+    while (rem >= ntd - te) {
+      rem -= ntd - te;
+      ++te;
+    }
+    const int tf = te + rem;
+    const int E0 = te * GT, F0 = tf * GT;
+    const int e = E0 + ty, f = F0 + tx;
+    const bool inside = e < nv && f < nv;
+    const double w = (te == tf) ? 1.0 : 2.0;
+    double at[OCT], ak[OCT];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    int e = E0 + ty + 8 * r, f = F0 + tx;
-    if (e < nv && f < nv) {
-      part = fma(st[r], sk[r], part);
-      if (want_sig) sig[(long)D.out * nv2 + (long)e * nv + f] = sq * st[r];
+    for (int o = 0; o < OCT; ++o) {
+      at[o] = 0.0;
+      ak[o] = 0.0;
+    }
+    for (int u = 0; u < D.nslots; ++u) {
+      const double* T = tau + (long)(D.slot + u) * nv2;
+      const double* K = kap + (long)(D.slot + u) * nv2;
+      {
+        // transposed tile: tT[fl][el] = T[F0 + fl][E0 + el]
+        const int fr = F0 + ty, ec = E0 + tx;
+        const bool ok = fr < nv && ec < nv;
+        tT[ty][tx] = ok ? T[(long)fr * nv + ec] : 0.0;
+        tK[ty][tx] = ok ? K[(long)fr * nv + ec] : 0.0;
+      }
+      __syncthreads();
+      const double a = inside ? T[(long)e * nv + f] : 0.0;
+      const double b = inside ? K[(long)e * nv + f] : 0.0;
+      const double att = tT[tx][ty], btt = tK[tx][ty];
+      const double du = dg[u];
+#pragma unroll
+      for (int o = 0; o < OCT; ++o) {
+        if (o < oc) {
+          const double c = cd[u][o];
+          const double c2 = c * sgn[o] * du;
+          at[o] = fma(c, a, fma(c2, att, at[o]));
+          ak[o] = fma(c, b, fma(c2, btt, ak[o]));
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int o = 0; o < OCT; ++o) {
+      if (o < oc) {
+        const double l = lam[o];
+        if (inside) part = fma(0.5 * l * w * at[o], ak[o], part);
+        if (want_sig) {
+          const double v = sqrt(fabs(l)) * at[o];
+          double* S = sig + (long)(D.out + D.o_begin + o) * nv2;
+          if (inside) S[(long)e * nv + f] = v;
+          if (te != tf) {
+            sA[ty][tx] = v;
+            __syncthreads();
+            const int fr = F0 + ty, ec = E0 + tx;  // S[f][e] = sgn S[e][f]
+            if (fr < nv && ec < nv) S[(long)fr * nv + ec] = sgn[o] * sA[tx][ty];
+            __syncthreads();
+          }
+        }
+      }
     }
   }
-  // warp then block reduction, fixed order
   for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-  if (tx == 0) red[ty] = part;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < DNT / 32; ++w) s += red[w];
-    e_part[(long)blockIdx.y * gridDim.x + blockIdx.x] = 0.5 * l * s;
-    if (want_sig && blockIdx.x == 0) sig_sign[D.out] = (l >= 0.0) ? 1.0 : -1.0;
+    for (int wv = 0; wv < GNT / 32; ++wv) s += red[wv];
+    e_part[(long)blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
+  if (want_sig && blockIdx.x == 0 && threadIdx.x < oc)
+    sig_sign[D.out + D.o_begin + threadIdx.x] = (lam[threadIdx.x] >= 0.0) ? 1.0 : -1.0;
 }
 
 // aa block of G in the swap-symmetric (sym) and swap-antisymmetric (anti) bases
@@ -247,15 +177,22 @@ __global__ void ordered_sum_kernel(const double* __restrict__ x, long n, double*
 
 }  // namespace
 
-int dress_f64(const Geometry& g, const DressDesc* d_desc, int ndesc, const DressAux& aux, const double* tau,
-              const double* kap, double* sig, double* sig_sign, double* e_part, bool want_sig,
+// Work items [0, ncc) are core-core groups (at most two outputs, one slot).
+int dress_f64(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, const DressAux& aux,
+              const double* tau, const double* kap, double* sig, double* sig_sign, double* e_part, bool want_sig,
               cudaStream_t st) {
-  if (ndesc <= 0) return DSRG_FNO_OK;
-  const int ntd = ceil_div(g.nv, DT);
-  dim3 grid(ntd * ntd, ndesc);
-  dress_kernel<<<grid, DNT, 0, st>>>(g.nv, g.na, d_desc, aux, tau, kap, sig, sig_sign, e_part,
-                                     want_sig ? 1 : 0);
-  DSRG_LAUNCH_CHECK();
+  if (ncc > 0) {
+    dim3 grid(DRESS_TILE_BLOCKS, ncc);
+    dress_kernel<2><<<grid, GNT, 0, st>>>(g.nv, g.na, d_desc, aux, tau, kap, sig, sig_sign, e_part,
+                                          want_sig ? 1 : 0);
+    DSRG_LAUNCH_CHECK();
+  }
+  if (ndesc > ncc) {
+    dim3 grid(DRESS_TILE_BLOCKS, ndesc - ncc);
+    dress_kernel<DRESS_OC><<<grid, GNT, 0, st>>>(g.nv, g.na, d_desc + ncc, aux, tau, kap, sig, sig_sign,
+                                                 e_part + (long)ncc * DRESS_TILE_BLOCKS, want_sig ? 1 : 0);
+    DSRG_LAUNCH_CHECK();
+  }
   return DSRG_FNO_OK;
 }
 

@@ -21,23 +21,27 @@ int gemm_f64(int M, int N, int K, double alpha, const double* A, long lda, bool 
 int pair_gemm_f64(const Geometry& g, const double* B, const double* eps, const int2* pairs,
                   int npairs, double* tau, double* kap, double* ts, cudaStream_t st);
 
-// Dressed matrices of one batch (see dress.cu).
+// Dressing work items of one batch (see dress.cu): outputs o_begin ..
+// o_begin + o_count - 1 of one hole-pair group whose slots are slot ..
+// slot + nslots - 1 and whose dressed matrices start at `out`.
 struct DressDesc {
-  int kind;      // DressKind
-  int slot;      // first Tau slot of the group in the batch
-  int a, b;      // kind-specific indices (eigenvector column, core index, ...)
-  int out;       // output index in Sig
+  int kind;     // DressKind
+  int slot, nslots;
+  int out;      // first dressed matrix of the group in the batch
+  int o_begin, o_count;
+  int m, pad;
 };
 
 enum DressKind {
-  DRESS_CC_DIAG = 0,   // sigma = tau^{mm},                lambda = 2
-  DRESS_CC_SYM = 1,    // (tau + tau^T)/sqrt2,              lambda = 2
-  DRESS_CC_ANTI = 2,   // (tau - tau^T)/sqrt2,              lambda = 6
-  DRESS_CA_SYM = 3,    // sum_u W[u][k] (t^{mu} + t^{muT})/sqrt2, lambda = g_k
-  DRESS_CA_ANTI = 4,   // ... with minus,                   lambda = 3 g_k
-  DRESS_AA_SYM = 5,    // eigvec k of the symmetric aa block
-  DRESS_AA_ANTI = 6    // eigvec k of the antisymmetric aa block
+  GROUP_CC_DIAG = 0,  // core pair (m, m): tau^{mm}, lambda 2
+  GROUP_CC_PAIR = 1,  // core pair m < n: (tau +- tau^T)/sqrt2, lambda 2 and 6
+  GROUP_CA = 2,       // core m with every active u: sum_u W[u][k] (tau^{mu} +- tau^{mu T})/sqrt2, g_k and 3 g_k
+  GROUP_AA = 3        // all active pairs: eigenvectors of the two swap blocks of the aa hole 2-RDM
 };
+
+// outputs per work item; blocks per work item (they stride over upper tiles)
+constexpr int DRESS_OC = 32;
+constexpr int DRESS_TILE_BLOCKS = 24;
 
 struct DressAux {
   const double* g1_evec;   // [na][na] (column k)
@@ -50,7 +54,7 @@ struct DressAux {
 };
 
 // sigma_r from tau (and kappa): energy partials and Sig_r = sqrt|lambda_r| sigma_r[tau].
-int dress_f64(const Geometry& g, const DressDesc* d_desc, int ndesc, const DressAux& aux,
+int dress_f64(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, const DressAux& aux,
               const double* tau, const double* kap, double* sig, double* sig_sign,
               double* e_part, bool want_sig, cudaStream_t st);
 
@@ -89,10 +93,18 @@ int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const
 // Fast form: exact bf16 digit planes on tcgen05 (sliced.cu)
 int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
                int* exps, cudaStream_t st);
+int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
+                  int* exps, cudaStream_t st);
 int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
-                     const int2* pairs, int npairs, bool energy_only, double* nu, int* err, cudaStream_t st);
-int pair_epilogue(const Geometry& g, const double* eps, const int2* pairs, int npairs, const double* nu,
-                  double* tau, double* kap, double* ts, cudaStream_t st);
+                     const int2* pairs, int npairs, bool energy_only, float2* nu, int* err, cudaStream_t st);
+// double-float elementwise stages (dd_stages.cu)
+int eps_to_dd(int n, const double* eps, float2* out, cudaStream_t st);
+int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd, const int2* pairs, int npairs,
+                     const float2* nu, float2* tau, float2* kap, double* ts, cudaStream_t st);
+int dress_dd(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, const DressAux& aux,
+             const float2* tau, const float2* kap, float2* sig, double* sig_sign, double* e_part, bool want_sig,
+             cudaStream_t st);
+int regularize_test(int n, const double* delta, double s, double* r1, double* y, cudaStream_t st);
 int sliced_syrk(int KS, int nv, int nr, const __nv_bfloat16* planes, const int* exps, int Kpad,
                 const double* sign, double* dpart, int nsplit, double* D, int* err, cudaStream_t st);
 int sliced_plain_gemm(int KS, int M, int N, const __nv_bfloat16* pa, const int* ea, const __nv_bfloat16* pb,

@@ -73,13 +73,56 @@ __device__ __forceinline__ void digits_of(double v, int e_row, int* d) {
   d[0] = (int)X;
 }
 
+// Digits of a double-float value hi + lo with the same rule: X = round((hi +
+// lo) 2^(F - e_row)), formed exactly in 64-bit fixed point with 16 guard bits.
+__device__ __forceinline__ long long fixed_of_float(float v, int e_row, int F, int G) {
+  const int b = __float_as_int(v);
+  const int E = (b >> 23) & 0xFF;
+  if (E == 0) return 0;
+  const long long m = (long long)((b & 0x7FFFFF) | 0x800000);
+  // v = m 2^(E-150); scaled by 2^(F - e_row + G)
+  const int sh = E - 150 + F - e_row + G;
+  long long x;
+  if (sh >= 0) x = sh < 39 ? (m << sh) : 0;  // sh < 39 always holds for |v| < 2^e_row
+  else x = (-sh < 63) ? (m >> (-sh)) : 0;
+  return b < 0 ? -x : x;
+}
+
+template <int KS>
+__device__ __forceinline__ void digits_of(float2 v, int e_row, int* d) {
+  constexpr int F = 7 + 8 * (KS - 1);
+  constexpr int G = 16;
+  long long Xg = fixed_of_float(v.x, e_row, F, G) + fixed_of_float(v.y, e_row, F, G);
+  long long X = Xg >= 0 ? ((Xg + (1LL << (G - 1))) >> G) : -((-Xg + (1LL << (G - 1))) >> G);
+#pragma unroll
+  for (int s = KS - 1; s >= 1; --s) {
+    long long r = ((X + 128) & 255) - 128;
+    d[s] = (int)r;
+    X = (X - r) >> 8;
+  }
+  d[0] = (int)X;
+}
+
+__device__ __forceinline__ double magnitude(double v) { return fabs(v); }
+__device__ __forceinline__ double magnitude(float2 v) { return (double)fabsf(v.x); }
+__device__ __forceinline__ int row_exponent_of(double mx, double) { return row_exponent(mx); }
+__device__ __forceinline__ int row_exponent_of(double mx, float2) {
+  // from the float hi parts: max |hi| < 2^e implies |hi + lo| < 2^e
+  const int b = __float_as_int((float)mx);
+  const int E = (b >> 23) & 0xFF;
+  return E == 0 ? -126 : E - 126;
+}
+__device__ __forceinline__ double zero_of(double) { return 0.0; }
+__device__ __forceinline__ float2 zero_of(float2) { return make_float2(0.f, 0.f); }
+
 // planes[s][row][k] (bf16, k padded to Kpad with zeros), exps[row].
 // Source element (row, k) at src[row * rs + k * ks]; one of rs, ks is 1.
-template <int KS>
-__global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ src, long R, int K, long rs,
+// T is double (float64 rows) or float2 (double-float rows).
+template <int KS, typename T>
+__global__ void __launch_bounds__(256) slice_rows_kernel(const T* __restrict__ src, long R, int K, long rs,
                                                          long ks, int Kpad, __nv_bfloat16* __restrict__ planes,
                                                          int* __restrict__ exps) {
-  __shared__ double tile[32][33];
+  __shared__ T tile[32][33];
   __shared__ int s_exp[32];
   const long row0 = (long)blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -92,19 +135,19 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
       int r = kfast ? ty + 8 * i : tx;
       int k = kfast ? tx : ty + 8 * i;
       long row = row0 + r;
-      double v = 0.0;
+      T v = zero_of(T());
       if (row < R && k0 + k < K) v = src[row * rs + (long)(k0 + k) * ks];
       tile[r][k] = v;
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) mx = fmax(mx, fabs(tile[myrow][part * 4 + j]));
+    for (int j = 0; j < 4; ++j) mx = fmax(mx, magnitude(tile[myrow][part * 4 + j]));
     __syncthreads();
   }
 #pragma unroll
   for (int o = 4; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (part == 0) {
-    int e = row_exponent(mx);
+    int e = row_exponent_of(mx, T());
     s_exp[myrow] = e;
     if (row0 + myrow < R) exps[row0 + myrow] = e;
   }
@@ -117,7 +160,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
       int r = kfast ? ty + 8 * i : tx;
       int k = kfast ? tx : ty + 8 * i;
       long rr = row0 + r;
-      double v = 0.0;
+      T v = zero_of(T());
       if (rr < R && k0 + k < K) v = src[rr * rs + (long)(k0 + k) * ks];
       tile[r][k] = v;
     }
@@ -169,7 +212,7 @@ struct GemmParams {
   // pair mode
   const int2* pairs;
   int np, na, energy_only;
-  double* nu_out;   // [slot][np][np]
+  float2* nu_out;   // [slot][np][np], double-float
   // plain mode: C[m][n] = A[m] . B[n] (rows M x N), exps of A and B separately
   int M, N;
   const int* exps_b;
@@ -488,13 +531,13 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
         const int a = mt * BM + row;
         if (a < P.np) {
           const int ea = P.exps[(long)pr.x * P.np + a];
-          double* out = P.nu_out + ((long)slot * P.np + a) * P.np;
+          float2* out = P.nu_out + ((long)slot * P.np + a) * P.np;
 #pragma unroll
           for (int c = 0; c < BN; ++c) {
             const int b = nt * BN + c;
             if (b < P.np && !(a < P.na && b < P.na)) {
-              const int eb = P.exps[(long)pr.y * P.np + b];
-              out[b] = ldexp((double)hi[c] + (double)lo[c], ea + eb);
+              const int sc = ea + P.exps[(long)pr.y * P.np + b];
+              out[b] = make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));  // double-float nu
             }
           }
         }
@@ -527,37 +570,6 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
   __syncthreads();
   tc::tc_fence_after();
   if (warp == 1) tc::tmem_dealloc(tmem, C::TMEM_COLS);
-}
-
-// --------------------------------------------- regulariser on the nu tiles
-// tau/kappa (vv) and t^{ij}_{ex} (va / av) from nu[slot][a][b], Eq. A7.
-__global__ void pair_epilogue_kernel(Geometry g, const double* __restrict__ eps, const int2* __restrict__ pairs,
-                                     const double* __restrict__ nu, double* __restrict__ tau,
-                                     double* __restrict__ kap, double* __restrict__ ts) {
-  const int slot = blockIdx.y;
-  const long n2 = (long)g.np * g.np;
-  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (idx >= n2) return;
-  const int a = (int)(idx / g.np), b = (int)(idx % g.np);
-  const int na = g.na, nv = g.nv;
-  const bool av = a >= na, bv = b >= na;
-  if (!av && !bv) return;
-  if (ts == nullptr && !(av && bv)) return;
-  const int2 pr = pairs[slot];
-  const int i = pr.x, j = pr.y;
-  const double* ep = eps + g.nc;
-  const double n = nu[(long)slot * n2 + idx];
-  const double delta = eps[i] + eps[j] - ep[a] - ep[b];
-  const double t = n * regularizer(delta, g.s);
-  if (av && bv) {
-    const long o = ((long)slot * nv + (a - na)) * nv + (b - na);
-    tau[o] = t;
-    kap[o] = 2.0 * n - delta * t;
-  } else if (av) {
-    ts[(((long)i * g.nh + j) * nv + (a - na)) * na + b] = t;
-  } else if (i != j) {
-    ts[(((long)j * g.nh + i) * nv + (b - na)) * na + a] = t;
-  }
 }
 
 // D[e][f] += sum_split dpart[split][min(e,f)][max(e,f)]
@@ -671,23 +683,34 @@ int tile_n_for(int KS) { return KS == 5 ? 48 : 64; }
 }  // namespace
 
 // ------------------------------------------------------------ public (lib)
-int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
-               int* exps, cudaStream_t st) {
+template <typename T>
+static int slice_rows_t(int KS, const T* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
+                        int* exps, cudaStream_t st) {
   if (R <= 0) return DSRG_FNO_OK;
   const int grid = (int)((R + 31) / 32);
   switch (KS) {
-    case 3: slice_rows_kernel<3><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
-    case 4: slice_rows_kernel<4><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
-    case 5: slice_rows_kernel<5><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
+    case 3: slice_rows_kernel<3, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
+    case 4: slice_rows_kernel<4, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
+    case 5: slice_rows_kernel<5, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
     default: return DSRG_FNO_ERR_ARG;
   }
   DSRG_LAUNCH_CHECK();
   return DSRG_FNO_OK;
 }
 
+int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
+               int* exps, cudaStream_t st) {
+  return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, st);
+}
+
+int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
+                  int* exps, cudaStream_t st) {
+  return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, st);
+}
+
 // nu[slot][a][b] for the listed pairs from B planes ([KS][nh*np][Kpad]).
 int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
-                     const int2* pairs, int npairs, bool energy_only, double* nu, int* err, cudaStream_t st) {
+                     const int2* pairs, int npairs, bool energy_only, float2* nu, int* err, cudaStream_t st) {
   GemmParams P{};
   P.mode = MODE_PAIR;
   P.nkb = Kpad / BKE;
@@ -704,16 +727,6 @@ int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, con
   P.err = err;
   const long rows = (long)g.nh * g.np;
   return dispatch_gemm(KS, planes, rows, planes, rows, Kpad, P, st);
-}
-
-int pair_epilogue(const Geometry& g, const double* eps, const int2* pairs, int npairs, const double* nu, double* tau,
-                  double* kap, double* ts, cudaStream_t st) {
-  if (npairs <= 0) return DSRG_FNO_OK;
-  const long n2 = (long)g.np * g.np;
-  dim3 grid(ceil_div(n2, 256), npairs);
-  pair_epilogue_kernel<<<grid, 256, 0, st>>>(g, eps, pairs, nu, tau, kap, ts);
-  DSRG_LAUNCH_CHECK();
-  return DSRG_FNO_OK;
 }
 
 // D += sum_r sign_r Sig_r Sig_r^T from Sig planes ([KS][nr*nv][Kpad]).
