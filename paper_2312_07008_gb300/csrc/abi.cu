@@ -316,9 +316,9 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
   b += doubles(want_d ? (size_t)nsplit * nv2 : 1);
   b += doubles(want_d && na ? (size_t)g.nh * g.nh * g.nv * na : 1);
   b += doubles(8);
-  b += 3 * doubles((size_t)na * na + 1) + doubles(2 * (size_t)na * na + 8);
-  b += 2 * doubles((size_t)ns * ns + 1) + doubles(2 * (size_t)ns * ns + 8);
-  b += 2 * doubles((size_t)nd * nd + 1) + doubles(2 * (size_t)nd * nd + 8);
+  b += 3 * doubles((size_t)na * na + 1) + doubles(eig_work_doubles(na));
+  b += 2 * doubles((size_t)ns * ns + 1) + doubles(eig_work_doubles(ns));
+  b += 2 * doubles((size_t)nd * nd + 1) + doubles(eig_work_doubles(nd));
   b += ws_bytes(8, sizeof(int));
   if (ks) {
     const size_t rows = (size_t)g.nh * g.np;
@@ -349,14 +349,14 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
   W.e_acc = ws_take<double>(ws, 8);
   W.g1A = ws_take<double>(ws, (size_t)na * na + 1);
   W.g1V = ws_take<double>(ws, (size_t)na * na + 1);
-  W.g1W = ws_take<double>(ws, 2 * (size_t)na * na + 8);
+  W.g1W = ws_take<double>(ws, eig_work_doubles(na));
   (void)ws_take<double>(ws, (size_t)na * na + 1);
   W.MsA = ws_take<double>(ws, (size_t)ns * ns + 1);
   W.MsV = ws_take<double>(ws, (size_t)ns * ns + 1);
-  W.MsW = ws_take<double>(ws, 2 * (size_t)ns * ns + 8);
+  W.MsW = ws_take<double>(ws, eig_work_doubles(ns));
   W.MaA = ws_take<double>(ws, (size_t)nd * nd + 1);
   W.MaV = ws_take<double>(ws, (size_t)nd * nd + 1);
-  W.MaW = ws_take<double>(ws, 2 * (size_t)nd * nd + 8);
+  W.MaW = ws_take<double>(ws, eig_work_doubles(nd));
   W.status = ws_take<int>(ws, 8);
   W.nsplit = nsplit;
   if (!W.status) return DSRG_FNO_ERR_NOMEM;
@@ -548,13 +548,13 @@ int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double thre
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
   const size_t n2 = (size_t)nvir * nvir;
-  DSRG_TRY(ws_reserve(ws, 2 * doubles(n2) + doubles(2 * n2 + 8) + ws_bytes(nvir + 8, sizeof(int))));
+  DSRG_TRY(ws_reserve(ws, 2 * doubles(n2) + doubles(eig_work_doubles(nvir)) + ws_bytes(nvir + 8, sizeof(int))));
   double* A = ws_take<double>(ws, n2);
   double* V = ws_take<double>(ws, n2);
-  double* work = ws_take<double>(ws, 2 * n2 + 8);
+  double* work = ws_take<double>(ws, eig_work_doubles(nvir));
   int* ib = ws_take<int>(ws, nvir + 8);
-  int* status = ib;
-  int* nk = ib + 1;
+  int* status = ib;  // four words
+  int* nk = ib + 4;
   int* rank = ib + 8;
   DSRG_CUDA(cudaMemcpyAsync(A, dvv, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   DSRG_PHASE("phase_no_eigen", st);
@@ -603,7 +603,7 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
   const int nk = nkept, nv = g.nv;
   const size_t nk2 = (size_t)nk * nk;
   const long rows = (long)g.nq * g.nh;
-  size_t fixed = ws_bytes(8, sizeof(int)) + doubles((size_t)nv * nk) * 2 + doubles(nk2) * 3 + doubles(2 * nk2 + 8) +
+  size_t fixed = ws_bytes(8, sizeof(int)) + doubles((size_t)nv * nk) * 2 + doubles(nk2) * 3 + doubles(eig_work_doubles(nk)) +
                  ws_bytes(nk + 8, sizeof(int)) + doubles((size_t)rows * gf.np + 1) + doubles(g.nh + nk + 1) +
                  doubles(nk + 1);
   const int ks = slices_of(prob);
@@ -623,7 +623,7 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
   double* F = ws_take<double>(ws, nk2);
   double* FV = ws_take<double>(ws, nk2);
   double* Wsort = ws_take<double>(ws, nk2);
-  double* work = ws_take<double>(ws, 2 * nk2 + 8);
+  double* work = ws_take<double>(ws, eig_work_doubles(nk));
   int* ib = ws_take<int>(ws, nk + 8);
   double* Bf = ws_take<double>(ws, (size_t)rows * gf.np + 1);
   double* epsf = ws_take<double>(ws, g.nh + nk + 1);

@@ -1,139 +1,274 @@
-// Float64 symmetric eigensolver (Eq. 8: Gamma V = n V) and helpers.
+// Symmetric eigensolver (Eq. 8: Gamma V = n V) and helpers.
 //
 // Cyclic two-sided Jacobi with round-robin pair ordering: in each round the
-// indices form n/2 disjoint pairs, so A' = J^T A J and V' = V J are computed
-// out of place in one launch, every output element reading the 2 x 2
-// neighbourhood it depends on.  Rotation angles follow the classical
-// symmetric Schur decomposition (Golub and Van Loan, "Matrix Computations",
-// Sec. 8.5): tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau)/(|tau| +
-// sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c.  Sweeps repeat until the
-// off-diagonal Frobenius norm falls below 1e-15 of the total.
+// indices form m/2 disjoint pairs (m = n rounded up to even, a padding index
+// never rotates), so A' = J^T A J and V' = V J update every 2 x 2 block of A
+// and every column pair of V independently.  The rotation of a pair (p, q)
+// annihilates a_pq: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) / (|tau| +
+// sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c (Golub and Van Loan, "Matrix
+// Computations", Sec. 8.5).
+//
+// GB300 runs float64 at a small fraction of its float32 rate, so the matrix
+// and the vectors are kept in double-float (hi + lo float32 pairs, ~48 bits)
+// and all rounds and sweeps run in one cooperative launch, separated by a
+// grid barrier whose waits are bounded.  t is formed in float32 from the
+// double-float difference a_qq - a_pp; c and s are then formed in
+// double-float from that float t so that c^2 + s^2 = 1 to double-float
+// accuracy: the rotation is orthogonal to working precision even where t
+// is not the exact annihilating angle, and the next sweep removes what is
+// left of a_pq.  A is double-buffered (every block of A' reads four entries
+// of A); V is updated in place (a thread owns a column pair).
+#include "dd.cuh"
 #include "kernels.h"
 
 namespace dsrg {
 
 namespace {
 
-constexpr int ET = 32;   // tile edge of the update kernel
-constexpr int ENT = 256; // threads per update block
+constexpr int JNT = 256;                 // threads per block
+constexpr int JMAX_BLOCKS = EIG_MAX_BLOCKS;
+constexpr long long BAR_SPIN_LIMIT = 20000000;  // ~2 s of 100 ns naps
 
-// partner of index i in round r of the round-robin schedule over m (even) slots
-__device__ __forceinline__ int rr_partner(int i, int r, int m) {
-  // slot position: index 0 fixed; index k>0 sits at position ((k - 1 - r) mod (m-1)) + 1
-  int pos;
-  if (i == 0) pos = 0;
-  else pos = ((i - 1 - r) % (m - 1) + (m - 1)) % (m - 1) + 1;
-  int ppos = m - 1 - pos;  // positions pos and m-1-pos face each other
-  if (ppos == 0) return 0;
-  return ((ppos - 1 + r) % (m - 1)) + 1;
+// index at position pos of round r (position 0 fixed, the others rotate)
+__device__ __forceinline__ int rr_index(int pos, int r, int m) {
+  return pos == 0 ? 0 : ((pos - 1 + r) % (m - 1)) + 1;
 }
 
-struct Rot {
-  int k2;     // partner index (or -1)
-  double w1;  // J[i][i]
-  double w2;  // J[partner][i]
+struct JacobiArgs {
+  int n, m;
+  const double* A_in;
+  double* A_out;  // full matrix: diagonal = eigenvalues
+  double* V_out;
+  float2* A0;     // double-float ping-pong buffers, n x n
+  float2* A1;
+  float2* V;      // double-float, n x n
+  double* red;    // 2 * gridDim.x partial norms
+  unsigned* bar;  // [0] arrivals, [1] generation
+  int* status;    // [0] 1 = no convergence, [1] 1 = barrier wait expired, [2] sweeps
+  int max_sweeps;
 };
 
-__device__ __forceinline__ Rot make_rot(const double* A, int n, int i, int r, int m) {
-  Rot R;
-  int q = rr_partner(i, r, m);
-  if (q >= n || q == i) {
-    R.k2 = -1;
-    R.w1 = 1.0;
-    R.w2 = 0.0;
-    return R;
-  }
-  int p = min(i, q), qq = max(i, q);
-  double apq = A[(long)p * n + qq];
-  double c = 1.0, s = 0.0;
-  if (apq != 0.0) {
-    double app = A[(long)p * n + p], aqq = A[(long)qq * n + qq];
-    double tau = (aqq - app) / (2.0 * apq);
-    double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-    c = 1.0 / sqrt(1.0 + t * t);
-    s = t * c;
-  }
-  // J = [[c, s], [-s, c]] on (p, q):  J[p][p] = c, J[q][p] = -s, J[p][q] = s, J[q][q] = c
-  R.k2 = q;
-  R.w1 = c;
-  R.w2 = (i == p) ? -s : s;
-  return R;
-}
-
-// One round: Aout = J^T A J, Vout = V J.  Grid: tiles of A then tiles of V.
-__global__ void __launch_bounds__(ENT) jacobi_round_kernel(int n, int m, int r, const double* __restrict__ A,
-                                                           double* __restrict__ Aout,
-                                                           const double* __restrict__ V,
-                                                           double* __restrict__ Vout,
-                                                           const int* __restrict__ done) {
-  if (*done) return;
-  __shared__ Rot rrow[ET], rcol[ET];
-  const int nt = (n + ET - 1) / ET;
-  int tile = blockIdx.x;
-  const bool isV = tile >= nt * nt;
-  if (isV) tile -= nt * nt;
-  const int i0 = (tile / nt) * ET, j0 = (tile % nt) * ET;
-  if (threadIdx.x < ET) {
-    int i = i0 + threadIdx.x;
-    if (i < n) rrow[threadIdx.x] = make_rot(A, n, i, r, m);
-  } else if (threadIdx.x < 2 * ET) {
-    int j = j0 + threadIdx.x - ET;
-    if (j < n) rcol[threadIdx.x - ET] = make_rot(A, n, j, r, m);
-  }
+// Grid barrier (all blocks are co-resident: cooperative launch).  Returns
+// false once any block's wait has expired; the kernel then returns.
+__device__ bool grid_barrier(const JacobiArgs& P) {
   __syncthreads();
-  for (int e = threadIdx.x; e < ET * ET; e += ENT) {
-    const int ti = e / ET, tj = e % ET;
-    const int i = i0 + ti, j = j0 + tj;
-    if (i >= n || j >= n) continue;
-    const Rot cj = rcol[tj];
-    if (isV) {
-      double v = cj.w1 * V[(long)i * n + j];
-      if (cj.k2 >= 0) v += cj.w2 * V[(long)i * n + cj.k2];
-      Vout[(long)i * n + j] = v;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = P.bar + 1;
+    volatile int* st = P.status + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = *st == 0;
+    if (atomicAdd(P.bar, 1u) == gridDim.x - 1) {
+      atomicExch(P.bar, 0u);
+      __threadfence();
+      atomicAdd(P.bar + 1, 1u);
     } else {
-      const Rot ci = rrow[ti];
-      // the rotated pair's off-diagonal element is annihilated
-      if (ci.k2 == j) {
-        Aout[(long)i * n + j] = 0.0;
-        continue;
+      long long it = 0;
+      while (ok && *gen == g) {
+        if (++it > BAR_SPIN_LIMIT || *st != 0) {
+          atomicExch(P.status + 1, 1);
+          ok = 0;
+        }
+        __nanosleep(100);
       }
-      double a11 = A[(long)i * n + j];
-      double v = ci.w1 * cj.w1 * a11;
-      if (cj.k2 >= 0) v += ci.w1 * cj.w2 * A[(long)i * n + cj.k2];
-      if (ci.k2 >= 0) {
-        v += ci.w2 * cj.w1 * A[(long)ci.k2 * n + j];
-        if (cj.k2 >= 0) v += ci.w2 * cj.w2 * A[(long)ci.k2 * n + cj.k2];
-      }
-      Aout[(long)i * n + j] = v;
     }
+    __threadfence();
+    s_ok = ok && *st == 0;
   }
+  __syncthreads();
+  return s_ok != 0;
 }
 
-// off-diagonal and total squared norms -> done flag (single block)
-__global__ void jacobi_check_kernel(int n, const double* __restrict__ A, int* done, double* norms) {
-  __shared__ double s_off[256], s_tot[256];
-  double off = 0.0, tot = 0.0;
-  for (long idx = threadIdx.x; idx < (long)n * n; idx += blockDim.x) {
-    double a = A[idx];
-    tot += a * a;
-    if (idx / n != idx % n) off += a * a;
+__device__ __forceinline__ dd ldd(const float2* p, long i) {
+  const float2 v = __ldcg(p + i);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void sdd(float2* p, long i, dd v) { __stcg(p + i, make_float2(v.hi, v.lo)); }
+
+// c a +- s b with double-float operands.  The sum keeps an absolute error
+// of a few units of 2^-48 max(|c a|, |s b|), which is what the backward
+// stability of the rotations needs (no relative accuracy under cancellation).
+__device__ __forceinline__ dd rot_combine(dd ca, dd a, dd sb, dd b, bool minus) {
+  const dd x = dd_mul(ca, a);
+  dd y = dd_mul(sb, b);
+  if (minus) y = dd_neg(y);
+  dd t = two_sum(x.hi, y.hi);
+  t.lo = __fadd_rn(t.lo, __fadd_rn(x.lo, y.lo));
+  return quick_two_sum(t.hi, t.lo);
+}
+
+// 1 / sqrt(x) for x in [1, 2] in double-float: float estimate, two Newton steps
+__device__ __forceinline__ dd dd_rsqrt12(dd x) {
+  dd y = dd_make(rsqrtf(x.hi));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const dd e = dd_sub(dd_make(1.0f), dd_mul(x, dd_mul(y, y)));
+    y = dd_add_f(y, 0.5f * y.hi * e.hi);
   }
-  s_off[threadIdx.x] = off;
-  s_tot[threadIdx.x] = tot;
+  return y;
+}
+
+// squared off-diagonal and total Frobenius norms of A (fixed summation order)
+__device__ void norms(const JacobiArgs& P, const float2* A, double* off, double* tot) {
+  __shared__ double s_o[JNT], s_t[JNT];
+  double o = 0.0, t = 0.0;
+  const long n2 = (long)P.n * P.n;
+  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+    const float2 v = __ldcg(A + idx);
+    const double a = (double)v.x + (double)v.y;
+    t += a * a;
+    if (idx / P.n != idx % P.n) o += a * a;
+  }
+  s_o[threadIdx.x] = o;
+  s_t[threadIdx.x] = t;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+  for (int w = JNT / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
-      s_off[threadIdx.x] += s_off[threadIdx.x + w];
-      s_tot[threadIdx.x] += s_tot[threadIdx.x + w];
+      s_o[threadIdx.x] += s_o[threadIdx.x + w];
+      s_t[threadIdx.x] += s_t[threadIdx.x + w];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    norms[0] = s_off[0];
-    norms[1] = s_tot[0];
-    // rounding floor of a converged sweep is about (n eps)^2 relative
-    const double tol = fmax(1e-30, (2.2e-16 * n) * (2.2e-16 * n));
-    if (s_off[0] <= tol * s_tot[0] || s_tot[0] == 0.0) *done = 1;
+    __stcg(P.red + 2 * blockIdx.x, s_o[0]);
+    __stcg(P.red + 2 * blockIdx.x + 1, s_t[0]);
+  }
+  if (!grid_barrier(P)) {
+    *off = -1.0;
+    return;
+  }
+  double so = 0.0, st = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    so += __ldcg(P.red + 2 * b);
+    st += __ldcg(P.red + 2 * b + 1);
+  }
+  *off = so;
+  *tot = st;
+}
+
+__global__ void __launch_bounds__(JNT) jacobi_coop_kernel(JacobiArgs P) {
+  extern __shared__ float4 s_cs[];  // per pair of the round: c (hi, lo), s (hi, lo)
+  const int n = P.n, m = P.m, half = m / 2;
+  const long n2 = (long)n * n;
+  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+    const dd a = dd_from_double(P.A_in[idx]);
+    sdd(P.A0, idx, a);
+    sdd(P.V, idx, dd_make(idx / n == idx % n ? 1.0f : 0.0f));
+  }
+  if (!grid_barrier(P)) return;
+  float2* A = P.A0;
+  float2* B = P.A1;
+  // rounding floor of a converged double-float sweep, relative and squared
+  const double tol = fmax(1e-30, ((double)n * 4e-15) * ((double)n * 4e-15));
+  double prev = -1.0;
+  int converged = 0, sweeps_done = 0;
+  for (int sweep = 0; sweep <= P.max_sweeps; ++sweep) {
+    sweeps_done = sweep;
+    double off, tot;
+    norms(P, A, &off, &tot);
+    if (off < 0.0) return;
+    if (tot == 0.0 || off <= tol * tot || (off <= 1e-22 * tot && prev >= 0.0 && off > 0.25 * prev)) {
+      converged = 1;
+      break;
+    }
+    prev = off;
+    if (sweep == P.max_sweeps) break;
+    for (int r = 0; r < m - 1; ++r) {
+      // rotation of every pair of this round (each block forms all of them)
+      for (int k = threadIdx.x; k < half; k += JNT) {
+        const int i1 = rr_index(k, r, m), i2 = rr_index(m - 1 - k, r, m);
+        const int p = min(i1, i2), q = max(i1, i2);
+        float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (q < n) {
+          const dd apq = dd_mul_f(dd_add(ldd(A, (long)p * n + q), ldd(A, (long)q * n + p)), 0.5f);
+          if (apq.hi != 0.0f) {
+            const dd d = dd_sub(ldd(A, (long)q * n + q), ldd(A, (long)p * n + p));
+            const float th = d.hi / (2.0f * apq.hi);
+            const float t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+            dd c = dd_rsqrt12(dd_add_f(two_prod(t, t), 1.0f));
+            dd sn = dd_mul_f(c, t);
+            // one first-order renormalisation: c^2 + s^2 = 1 to the last bits
+            const float g = dd_sub(dd_add(dd_mul(c, c), dd_mul(sn, sn)), dd_make(1.0f)).hi;
+            c = dd_add(c, dd_mul_f(c, -0.5f * g));
+            sn = dd_add(sn, dd_mul_f(sn, -0.5f * g));
+            cs = make_float4(c.hi, c.lo, sn.hi, sn.lo);
+          }
+        }
+        s_cs[k] = cs;
+      }
+      __syncthreads();
+      // work units: (row pair of A, column pair) for half row pairs, then
+      // (row of V, column pair) for n rows; consecutive units share a row
+      const long units = (long)(half + n) * half;
+      for (long u = blockIdx.x * (long)JNT + threadIdx.x; u < units; u += (long)gridDim.x * JNT) {
+        const int it = (int)(u / half), k = (int)(u % half);
+        const int j1 = rr_index(k, r, m), j2 = rr_index(m - 1 - k, r, m);
+        const int pc = min(j1, j2), qc = max(j1, j2);
+        const bool qcr = qc < n;
+        const float4 cc = s_cs[k];
+        const dd cR = {cc.x, cc.y}, sR = {cc.z, cc.w};
+        if (it < half) {
+          const int i1 = rr_index(it, r, m), i2 = rr_index(m - 1 - it, r, m);
+          const int p = min(i1, i2), q = max(i1, i2);
+          const float4 rc = s_cs[it];
+          const dd cP = {rc.x, rc.y}, sP = {rc.z, rc.w};
+          // M = A[{p,q}, {pc,qc}] J_R
+          const dd a_pp = ldd(A, (long)p * n + pc);
+          const dd a_pq = qcr ? ldd(A, (long)p * n + qc) : dd_make(0.f);
+          const dd m_p0 = qcr ? rot_combine(cR, a_pp, sR, a_pq, true) : a_pp;
+          const dd m_p1 = qcr ? rot_combine(sR, a_pp, cR, a_pq, false) : dd_make(0.f);
+          if (q < n) {
+            const dd a_qp = ldd(A, (long)q * n + pc);
+            const dd a_qq = qcr ? ldd(A, (long)q * n + qc) : dd_make(0.f);
+            const dd m_q0 = qcr ? rot_combine(cR, a_qp, sR, a_qq, true) : a_qp;
+            const dd m_q1 = qcr ? rot_combine(sR, a_qp, cR, a_qq, false) : dd_make(0.f);
+            // A' = J_P^T M
+            sdd(B, (long)p * n + pc, rot_combine(cP, m_p0, sP, m_q0, true));
+            sdd(B, (long)q * n + pc, rot_combine(sP, m_p0, cP, m_q0, false));
+            if (qcr) {
+              sdd(B, (long)p * n + qc, rot_combine(cP, m_p1, sP, m_q1, true));
+              sdd(B, (long)q * n + qc, rot_combine(sP, m_p1, cP, m_q1, false));
+            }
+          } else {
+            sdd(B, (long)p * n + pc, m_p0);
+            if (qcr) sdd(B, (long)p * n + qc, m_p1);
+          }
+        } else if (qcr) {
+          const int i = it - half;
+          const dd v0 = ldd(P.V, (long)i * n + pc), v1 = ldd(P.V, (long)i * n + qc);
+          sdd(P.V, (long)i * n + pc, rot_combine(cR, v0, sR, v1, true));
+          sdd(P.V, (long)i * n + qc, rot_combine(sR, v0, cR, v1, false));
+        }
+      }
+      if (!grid_barrier(P)) return;
+      float2* tmp = A;
+      A = B;
+      B = tmp;
+    }
+  }
+  // Columns of V drift from unit length by rounding of the rotations; with
+  // V = Vn N (N the column norms) the Rayleigh quotients become a_jj / N_j^2.
+  double* nrm2 = reinterpret_cast<double*>(B);  // the free ping-pong buffer (n^2 >= n doubles)
+  for (int j = blockIdx.x * JNT + threadIdx.x; j < n; j += gridDim.x * JNT) {
+    dd acc = dd_make(0.0f);
+    for (int i = 0; i < n; ++i) {
+      const dd v = ldd(P.V, (long)i * n + j);
+      acc = dd_add(acc, dd_mul(v, v));
+    }
+    __stcg(nrm2 + j, dd_to_double(acc));
+  }
+  if (!grid_barrier(P)) return;
+  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    const float2 a = __ldcg(A + idx), v = __ldcg(P.V + idx);
+    const double nj = __ldcg(nrm2 + j);
+    P.A_out[idx] = ((double)a.x + (double)a.y) / (i == j ? nj : sqrt(nj * __ldcg(nrm2 + i)));
+    P.V_out[idx] = ((double)v.x + (double)v.y) / sqrt(nj);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.status[0] = converged ? 0 : 1;
+    P.status[2] = sweeps_done;
   }
 }
 
@@ -197,48 +332,47 @@ __global__ void eig_permute_kernel(int n, const double* __restrict__ A, const do
 
 // A (n x n, symmetric) is destroyed: on return its diagonal holds the
 // eigenvalues; V (n x n) receives the eigenvectors (column j <-> A[j][j]).
-// work: 2 n^2 + 8 doubles.  status_dev: one int of device memory.
+// work: eig_work_doubles(n) doubles.  status_dev: four ints of device memory.
 int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
                    cudaStream_t st) {
   if (n <= 0) return DSRG_FNO_OK;
-  double* A2 = work;
-  double* V2 = work + (long)n * n;
-  double* norms = work + 2L * n * n;
-  long n2 = (long)n * n;
-  identity_kernel<<<ceil_div(n2, 256), 256, 0, st>>>(n, V);
-  DSRG_LAUNCH_CHECK();
-  DSRG_CUDA(cudaMemsetAsync(status_dev, 0, sizeof(int), st));
-  if (n == 1) return DSRG_FNO_OK;
   const int m = (n % 2 == 0) ? n : n + 1;
-  const int nt = ceil_div(n, ET);
-  double* a = A;
-  double* a2 = A2;
-  double* v = V;
-  double* v2 = V2;
-  int converged = 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    jacobi_check_kernel<<<1, 256, 0, st>>>(n, a, status_dev, norms);
-    DSRG_LAUNCH_CHECK();
-    DSRG_CUDA(cudaMemcpyAsync(&converged, status_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-    DSRG_CUDA(cudaStreamSynchronize(st));
-    if (converged) break;
-    for (int r = 0; r < m - 1; ++r) {
-      jacobi_round_kernel<<<2 * nt * nt, ENT, 0, st>>>(n, m, r, a, a2, v, v2, status_dev);
-      DSRG_LAUNCH_CHECK();
-      std::swap(a, a2);
-      std::swap(v, v2);
-    }
-  }
-  if (!converged) {
-    jacobi_check_kernel<<<1, 256, 0, st>>>(n, a, status_dev, norms);
-    DSRG_CUDA(cudaMemcpyAsync(&converged, status_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-    DSRG_CUDA(cudaStreamSynchronize(st));
-  }
-  if (a != A) {
-    DSRG_CUDA(cudaMemcpyAsync(A, a, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    DSRG_CUDA(cudaMemcpyAsync(V, v, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  }
-  return converged ? DSRG_FNO_OK : DSRG_FNO_ERR_NOCONV;
+  const long n2 = (long)n * n;
+  JacobiArgs P;
+  P.n = n;
+  P.m = m;
+  P.A_in = A;
+  P.A_out = A;
+  P.V_out = V;
+  P.A0 = reinterpret_cast<float2*>(work);
+  P.A1 = reinterpret_cast<float2*>(work + n2);
+  P.V = reinterpret_cast<float2*>(work + 2 * n2);
+  P.red = work + 3 * n2;
+  P.bar = reinterpret_cast<unsigned*>(work + 3 * n2 + 2 * JMAX_BLOCKS);
+  P.status = status_dev;
+  P.max_sweeps = max_sweeps;
+  DSRG_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
+  DSRG_CUDA(cudaMemsetAsync(status_dev, 0, 4 * sizeof(int), st));
+  const size_t smem = sizeof(float4) * (size_t)(m / 2);
+  if (smem > 200 * 1024) return DSRG_FNO_ERR_UNSUPPORTED;
+  DSRG_CUDA(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, occ = 0;
+  DSRG_CUDA(cudaGetDevice(&dev));
+  DSRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_coop_kernel, JNT, smem));
+  if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
+  // (half + n) * half work units per round; small matrices use few blocks
+  const long units = (long)(m / 2 + n) * (m / 2);
+  int nblk = (int)std::min<long>(std::min(sms * std::min(occ, 2), JMAX_BLOCKS), (units + 8 * JNT - 1) / (8 * JNT));
+  nblk = std::max(nblk, 1);
+  void* args[] = {&P};
+  DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(nblk), dim3(JNT), args, smem, st));
+  DSRG_LAUNCH_CHECK();
+  int h[2] = {0, 0};
+  DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  if (h[1]) return DSRG_FNO_ERR_TIMEOUT;
+  return h[0] ? DSRG_FNO_ERR_NOCONV : DSRG_FNO_OK;
 }
 
 // evals/evecs sorted (descending or ascending) from the Jacobi output;

@@ -63,6 +63,8 @@ int syrk_dressed_f64(int nv, int nr, const double* sig, const double* sig_sign, 
                      int nsplit, double* D, cudaStream_t st);
 
 // Symmetric-eigen helpers (eig.cu)
+constexpr int EIG_MAX_BLOCKS = 1024;  // grid bound of the eigensolver (reduction scratch)
+constexpr size_t eig_work_doubles(int n) { return 3 * (size_t)n * n + 2 * EIG_MAX_BLOCKS + 16; }
 int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
                    cudaStream_t st);
 int eig_sort(int n, const double* A, const double* V, double* evals, double* evecs, int* rank,

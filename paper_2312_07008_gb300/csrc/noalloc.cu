@@ -14,11 +14,11 @@
 
 namespace dsrg {
 
-// Largest nvir the array serves: A, V and the Jacobi work (4 n^2 doubles),
-// then status, N' and the sort ranks (n + 8 ints) in its tail.
+// Largest nvir the array serves: A, V and the eigensolver work, then status,
+// N' and the sort ranks (n + 8 ints) in its tail.
 constexpr int NOALLOC_NVIR_MAX = 512;
-constexpr size_t NOALLOC_DOUBLES =
-    4 * (size_t)NOALLOC_NVIR_MAX * NOALLOC_NVIR_MAX + 8 + (NOALLOC_NVIR_MAX + 8 + 1) / 2 + 1;
+constexpr size_t NOALLOC_DOUBLES = 2 * (size_t)NOALLOC_NVIR_MAX * NOALLOC_NVIR_MAX +
+                                   eig_work_doubles(NOALLOC_NVIR_MAX) + (NOALLOC_NVIR_MAX + 8 + 1) / 2 + 1;
 
 // Held by every device that loads the library, until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
@@ -66,13 +66,13 @@ extern "C" int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_
   const size_t n2 = (size_t)nvir * nvir;
   double* A = base;
   double* V = A + n2;
-  double* work = V + n2;  // 2 n^2 + 8
-  int* ib = reinterpret_cast<int*>(work + 2 * n2 + 8);
-  int* status = ib;
-  int* nk = ib + 1;
+  double* work = V + n2;
+  int* ib = reinterpret_cast<int*>(work + eig_work_doubles(nvir));
+  int* status = ib;  // four words
+  int* nk = ib + 4;
   int* rank = ib + 8;
   // Every scratch word read below is first written by this call: A is a copy
-  // of dvv, the Jacobi sets V to the identity and zeroes its status word.
+  // of dvv, the eigensolver initialises its own work and status words.
   DSRG_CUDA(cudaMemcpyAsync(A, dvv, n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   DSRG_TRY(eig_sym_jacobi(nvir, A, V, work, status, 60, st));
   DSRG_TRY(eig_sort(nvir, A, V, on_out, no_out, rank, true, true, st));

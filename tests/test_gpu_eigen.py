@@ -1,0 +1,88 @@
+"""The natural-orbital eigensolver (Eq. 8) behind dsrg_fno_truncate.
+
+Occupation numbers are the eigenvalues of D_vv in descending order and the
+natural orbitals its eigenvectors: checked against LAPACK (numpy.linalg.eigh)
+on matrices with odd and even sizes, exactly repeated eigenvalues, tight
+clusters, a wide spread of magnitudes and already-diagonal input.  Vectors
+are compared through the projectors onto the spans of groups of eigenvalues
+that are well separated from the rest (the basis inside a degenerate group
+is not unique).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2312_07008_gb300 as pkg  # noqa: E402
+
+
+def solve(D):
+    n = D.shape[0]
+    d = torch.tensor(D, dtype=torch.float64, device="cuda")
+    on = torch.empty(n, dtype=torch.float64, device="cuda")
+    no = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    pkg.dsrg_fno_truncate(n, d, pkg.MODE_PO, 99.0, 0.01, on, no)
+    return on.cpu().numpy(), no.cpu().numpy()
+
+
+def with_spectrum(rng, lam):
+    n = len(lam)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (Q * lam) @ Q.T
+
+
+def check(D, ons, nos, gap_rel=1e-6):
+    n = D.shape[0]
+    w, U = np.linalg.eigh(D)
+    w, U = w[::-1], U[:, ::-1]
+    scale = max(np.abs(w).max(), 1e-300)
+    assert np.all(np.diff(ons) <= 0.0)
+    np.testing.assert_allclose(ons, w, rtol=0, atol=1e-12 * scale)
+    assert np.abs(nos.T @ nos - np.eye(n)).max() < 1e-12
+    assert np.abs((nos * ons) @ nos.T - D).max() < 1e-12 * scale
+    # groups separated by relative gaps above gap_rel
+    cuts = [0] + [k + 1 for k in range(n - 1) if w[k] - w[k + 1] > gap_rel * scale] + [n]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        P = U[:, a:b] @ U[:, a:b].T
+        Q = nos[:, a:b] @ nos[:, a:b].T
+        # subspace error ~ (rounding of A) / (gap to the rest)
+        assert np.abs(P - Q).max() < 1e-14 / gap_rel + 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 65, 130, 257])
+def test_random_spectra(n):
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((n, n))
+    D = X + X.T
+    ons, nos = solve(D)
+    check(D, ons, nos)
+
+
+def test_repeated_and_clustered_eigenvalues():
+    rng = np.random.default_rng(5)
+    lam = np.concatenate([np.full(7, 2.5), np.full(5, 1e-3), 0.7 + 1e-13 * rng.standard_normal(6),
+                          rng.uniform(-1, 1, 45)])
+    D = with_spectrum(rng, lam)
+    D = 0.5 * (D + D.T)
+    ons, nos = solve(D)
+    check(D, ons, nos)
+
+
+def test_wide_magnitude_range_like_occupation_numbers():
+    rng = np.random.default_rng(6)
+    n = 301
+    lam = 10.0 ** rng.uniform(-9, 0.5, n)
+    D = with_spectrum(rng, lam)
+    D = 0.5 * (D + D.T)
+    ons, nos = solve(D)
+    check(D, ons, nos)
+
+
+def test_diagonal_input_needs_no_rotation():
+    lam = np.array([3.0, -1.0, 2.0, 0.5, 0.5, 7.0, 0.0])
+    ons, nos = solve(np.diag(lam))
+    np.testing.assert_array_equal(ons, np.sort(lam)[::-1])
+    assert np.abs(np.abs(nos).sum(axis=0) - 1.0).max() == 0.0
