@@ -122,8 +122,8 @@ int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold
  * through its own pool, or a latency-critical loop where an allocation, which
  * may synchronise the device, is not acceptable.  This call does the same
  * eigensolve and cut as dsrg_fno_truncate with the same arguments, but its
- * scratch is one fixed file-scope device array of the library (4 nvir^2
- * doubles for nvir up to 512, about 8 MB), held by every device that loads
+ * scratch is one fixed file-scope device array of the library (5 nvir^2
+ * doubles and a few KB for nvir up to 512, about 10.5 MB), held by every device that loads
  * the library until the process exits.
  *   - nvir > 512 returns DSRG_FNO_ERR_ARG (message on stderr).
  *   - The first call on a device looks up the array's device address on that
@@ -149,6 +149,56 @@ int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_t mode, dou
 int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept,
                                   const double* no, const double* e2_mo_in, double* de_out,
                                   double* e2_fno_out, double* eps_fno_out, void* stream);
+
+/* State-averaged densities of Eq. A1 from per-state spin-free densities,
+ * host arrays (a helper for preparing dsrg_fno_problem inputs):
+ *   w            [nstates] weights, each >= 0, summing to 1 (1e-12);
+ *   g1_states    [nstates][nact][nact], Gamma1_a[u][v] = sum_sigma <a+_u a_v>;
+ *   g2_states    [nstates][nact]^4, Gamma2_a[u][v][x][y] = sum_{sigma tau}
+ *                <a+_{u sigma} a+_{v tau} a_{y tau} a_{x sigma}>;
+ *   gamma1_out   [nact][nact]  = sum_a w_a Gamma1_a;
+ *   lambda2_out  [nact]^4      = Gamma2 - Gamma1[u][x] Gamma1[v][y]
+ *                               + 1/2 Gamma1[u][y] Gamma1[v][x],
+ *                with Gamma1, Gamma2 the averaged densities (the cumulant of
+ *                the ensemble, not an average of per-state cumulants).
+ * Returns DSRG_FNO_ERR_ARG for nact < 1, nstates < 1, a null pointer or bad
+ * weights.  No device work. */
+int dsrg_fno_sa_densities(int32_t nact, int32_t nstates, const double* w, const double* g1_states,
+                          const double* g2_states, double* gamma1_out, double* lambda2_out);
+
+/* One instance of a batched run (dsrg_fno_batch_run). */
+typedef struct {
+  dsrg_fno_problem problem;  /* inputs, as for the single-instance calls */
+  /* device [nvir][nvir]: D_vv (dsrg_fno_vv_opdm); NULL = energy only */
+  double* dvv_out;
+  /* natural orbitals and cut (dsrg_fno_truncate): cut_mode -1 = none, else
+   * 0/1/2 with cut_threshold and cut_degen_ratio; needs dvv_out, on_out
+   * (device [nvir]) and no_out (device [nvir][nvir]). */
+  int32_t cut_mode;
+  double cut_threshold, cut_degen_ratio;
+  double* on_out;
+  double* no_out;
+  /* 1: discarded-virtual correction of the cut (dsrg_fno_discarded_correction) */
+  int32_t correction;
+  /* outputs, written by the call */
+  double e2;      /* E_vv in the MO basis */
+  int32_t nkept;  /* N' of the cut (0 without one) */
+  double de;      /* E_vv(MO) - E_vv(FNO) (0 without a correction) */
+  int32_t status; /* dsrg_fno_status of this instance */
+} dsrg_fno_batch_item;
+
+/* Runs n independent instances (ragged sizes, each the pipeline of the
+ * single-instance calls it requests) concurrently on the current device:
+ * instances are taken largest first by nworkers host workers, each with its
+ * own CUDA stream and device workspace (a share of the free memory).  The
+ * work is ordered after what `stream` holds at the call; the call returns
+ * when every instance is done, and later work on `stream` is ordered after
+ * it.  nworkers 0 = autotuned: the first calls with a given batch shape try
+ * 2, 4 and 8 workers, later calls use the fastest.  Returns DSRG_FNO_OK
+ * when every instance succeeded, else the status of the first failing
+ * instance (in index order); each item carries its own status.  One batch
+ * at a time per process (calls are serialised). */
+int dsrg_fno_batch_run(dsrg_fno_batch_item* items, int32_t n, int32_t nworkers, void* stream);
 
 /* Human-readable text of a status code. */
 const char* dsrg_fno_status_string(int status);

@@ -4,8 +4,9 @@
  * While profiling is enabled, the library brackets every launch of its
  * tensor-core contraction kernel and of its float64 pair-contraction kernel
  * with CUDA events on the launching stream, and counts every kernel it
- * launches.  Queries synchronise on the recorded events.  Not thread-safe
- * with concurrent library calls on other threads.
+ * launches.  Queries synchronise on the recorded events.  Records of
+ * concurrent calls (the batch runner's workers) are summed: phase totals are
+ * then stream time, not wall time.
  */
 #ifndef DSRG_FNO_PROFILE_H
 #define DSRG_FNO_PROFILE_H
@@ -25,6 +26,9 @@ int dsrg_fno_profile_query(const char* name, double* total_ms, int64_t* launches
 /* Number of kernels the library launched since the last reset; `reset`
  * != 0 zeroes the counter after reading it. */
 int64_t dsrg_fno_launch_count(int32_t reset);
+
+/* Worker count the last dsrg_fno_batch_run used (0 before any). */
+int32_t dsrg_fno_batch_last_workers(void);
 
 #ifdef __cplusplus
 }

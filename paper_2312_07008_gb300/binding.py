@@ -22,6 +22,8 @@ EXPORTED = (
     "dsrg_fno_truncate_noalloc",
     "dsrg_fno_cut",
     "dsrg_fno_discarded_correction",
+    "dsrg_fno_sa_densities",
+    "dsrg_fno_batch_run",
     "dsrg_fno_status_string",
     "dsrg_fno_release",
     "dsrg_fno_debug_sliced_gemm",
@@ -31,6 +33,7 @@ EXPORTED = (
     "dsrg_fno_profile_enable",
     "dsrg_fno_profile_query",
     "dsrg_fno_launch_count",
+    "dsrg_fno_batch_last_workers",
 )
 
 FP64 = 0
@@ -54,6 +57,15 @@ class CProblem(ctypes.Structure):
     ]
 
 
+class CBatchItem(ctypes.Structure):
+    _fields_ = [
+        ("problem", CProblem), ("dvv_out", ctypes.c_void_p),
+        ("cut_mode", ctypes.c_int32), ("cut_threshold", ctypes.c_double), ("cut_degen_ratio", ctypes.c_double),
+        ("on_out", ctypes.c_void_p), ("no_out", ctypes.c_void_p), ("correction", ctypes.c_int32),
+        ("e2", ctypes.c_double), ("nkept", ctypes.c_int32), ("de", ctypes.c_double), ("status", ctypes.c_int32),
+    ]
+
+
 _lib = None
 
 
@@ -74,6 +86,11 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_cut.argtypes = [i32, vp, i32, d, d, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_discarded_correction.argtypes = [P, i32, vp, ctypes.POINTER(d), ctypes.POINTER(d),
                                                   ctypes.POINTER(d), vp, vp]
+    dp_ = ctypes.POINTER(d)
+    lib.dsrg_fno_sa_densities.argtypes = [i32, i32, dp_, dp_, dp_, dp_, dp_]
+    lib.dsrg_fno_batch_run.argtypes = [ctypes.POINTER(CBatchItem), i32, i32, vp]
+    lib.dsrg_fno_batch_last_workers.argtypes = []
+    lib.dsrg_fno_batch_last_workers.restype = i32
     lib.dsrg_fno_status_string.argtypes = [ctypes.c_int]
     lib.dsrg_fno_status_string.restype = ctypes.c_char_p
     lib.dsrg_fno_release.argtypes = []
@@ -91,7 +108,7 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_launch_count.argtypes = [i32]
     lib.dsrg_fno_launch_count.restype = ctypes.c_int64
     for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_truncate", "dsrg_fno_truncate_noalloc",
-              "dsrg_fno_cut", "dsrg_fno_discarded_correction"):
+              "dsrg_fno_cut", "dsrg_fno_discarded_correction", "dsrg_fno_sa_densities", "dsrg_fno_batch_run"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -184,6 +201,56 @@ def dsrg_fno_discarded_correction(prob: Problem, nkept, no, e2_mo=None, eps_fno_
            load().dsrg_fno_discarded_correction(ctypes.byref(prob.c), int(nkept), _ptr(no), emo, ctypes.byref(de),
                                                 ctypes.byref(ef), _ptr(eps_fno_out), _stream(stream)))
     return de.value, ef.value
+
+
+def dsrg_fno_sa_densities(weights, g1_states, g2_states):
+    """SA Gamma1 and the ensemble 2-cumulant (Eq. A1) from per-state host arrays."""
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    g1 = np.ascontiguousarray(np.asarray(g1_states, dtype=np.float64))
+    g2 = np.ascontiguousarray(np.asarray(g2_states, dtype=np.float64))
+    nst, n = g1.shape[0], g1.shape[1]
+    if g1.shape != (nst, n, n) or g2.shape != (nst, n, n, n, n) or w.shape != (nst,):
+        raise ValueError("shapes: weights [S], g1_states [S][n][n], g2_states [S][n]^4")
+    out1 = np.zeros((n, n))
+    out2 = np.zeros((n, n, n, n))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check("dsrg_fno_sa_densities",
+           load().dsrg_fno_sa_densities(n, nst, w.ctypes.data_as(dp), g1.ctypes.data_as(dp), g2.ctypes.data_as(dp),
+                                        out1.ctypes.data_as(dp), out2.ctypes.data_as(dp)))
+    return out1, out2
+
+
+def dsrg_fno_batch_run(problems, dvv_outs=None, cut=None, on_outs=None, no_outs=None, correction=False,
+                       nworkers=0, stream=None):
+    """Runs independent instances concurrently (dsrg_fno_batch_run).
+
+    problems: list of Problem; dvv_outs: list of device tensors or None
+    (energy only); cut: (mode, threshold, degen_ratio) or None, with on_outs
+    and no_outs; correction: discarded-virtual correction after the cut.
+    Returns a list of dicts (e2, nkept, de) in input order; raises on the
+    first failing instance (each status is in the 'status' key).
+    """
+    n = len(problems)
+    arr = (CBatchItem * max(n, 1))()
+    for i, p in enumerate(problems):
+        it = arr[i]
+        it.problem = p.c
+        it.dvv_out = _ptr(dvv_outs[i]) if dvv_outs is not None else None
+        if cut is not None:
+            it.cut_mode, it.cut_threshold, it.cut_degen_ratio = int(cut[0]), float(cut[1]), float(cut[2])
+            it.on_out = _ptr(on_outs[i])
+            it.no_out = _ptr(no_outs[i])
+        else:
+            it.cut_mode = -1
+        it.correction = 1 if correction else 0
+    st = load().dsrg_fno_batch_run(arr, n, int(nworkers), _stream(stream))
+    out = [dict(e2=arr[i].e2, nkept=arr[i].nkept, de=arr[i].de, status=arr[i].status) for i in range(n)]
+    _check("dsrg_fno_batch_run", st)
+    return out
+
+
+def dsrg_fno_batch_last_workers() -> int:
+    return load().dsrg_fno_batch_last_workers()
 
 
 def dsrg_fno_release():

@@ -215,7 +215,7 @@ static long pair_cap_for_budget(int nv, int np, int ks, size_t budget) {
   return std::max<long>(cap, 1);
 }
 
-static size_t device_budget() {
+size_t device_budget() {
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
@@ -428,70 +428,27 @@ static size_t energy_pass_bytes(const Geometry& g, int ks, size_t budget) {
   return pass_bytes(g, P, false, 1, ks);
 }
 
-}  // namespace dsrg
-
-using namespace dsrg;
-
-extern "C" {
-
-const char* dsrg_fno_status_string(int s) {
-  switch (s) {
-    case DSRG_FNO_OK: return "ok";
-    case DSRG_FNO_ERR_ARG: return "invalid argument";
-    case DSRG_FNO_ERR_CUDA: return "CUDA runtime error";
-    case DSRG_FNO_ERR_NOMEM: return "device workspace allocation failed";
-    case DSRG_FNO_ERR_NOCONV: return "eigensolver did not converge";
-    case DSRG_FNO_ERR_TIMEOUT: return "bounded device wait expired";
-    case DSRG_FNO_ERR_NONFINITE: return "non-finite input or result";
-    case DSRG_FNO_ERR_UNSUPPORTED: return "unsupported request";
-    default: return "unknown status";
-  }
-}
-
-void dsrg_fno_release(void) {
-  std::lock_guard<std::mutex> lk(workspace_mutex());
-  int cur = 0;
-  cudaGetDevice(&cur);
-  for (int d = 0; d < 64; ++d) {
-    if (g_ws[d].base) {
-      cudaSetDevice(d);
-      cudaDeviceSynchronize();
-      cudaFree(g_ws[d].base);
-      g_ws[d].base = nullptr;
-      g_ws[d].cap = 0;
-      g_ws[d].off = 0;
-    }
-  }
-  cudaSetDevice(cur);
-}
-
-int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stream) {
+int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* e2_out, cudaStream_t st) {
   int s = validate(prob);
   if (s) return s;
   if (!e2_out) return DSRG_FNO_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> lk(workspace_mutex());
-  Workspace& ws = workspace_for_current_device();
   const Geometry g = geometry_of(prob);
   const int ks = slices_of(prob);
-  const size_t budget = device_budget() + ws.cap / 2;
   DSRG_TRY(ws_reserve(ws, energy_pass_bytes(g, ks, budget) + ws_bytes(8, sizeof(int))));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
   return energy_pass(g, ks, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, ws.off, budget, e2_out, st);
 }
 
-int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out, void* stream) {
+int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
+                        cudaStream_t st) {
   int s = validate(prob);
   if (s) return s;
   if (!dvv_out || !is_device_ptr(dvv_out)) return DSRG_FNO_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> lk(workspace_mutex());
-  Workspace& ws = workspace_for_current_device();
   const Geometry g = geometry_of(prob);
   const int ks = slices_of(prob);
   Plan P;
-  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, device_budget() + ws.cap / 2), P);
+  build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, budget), P);
   const int nsplit = nsplit_for(g.nv, P.max_out);
   const size_t small = small_terms_work_doubles(g.nc, g.na, g.nv);
   const int kmax = small_terms_kmax(g.nc, g.na);
@@ -539,14 +496,11 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   return DSRG_FNO_OK;
 }
 
-int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,
-                      double* on_out, double* no_out, int32_t* nkept_out, void* stream) {
+int impl_truncate(Workspace& ws, int32_t nvir, const double* dvv, int32_t mode, double threshold,
+                         double degen_ratio, double* on_out, double* no_out, int32_t* nkept_out, cudaStream_t st) {
   if (nvir <= 0 || !dvv || !on_out || !no_out || !nkept_out) return DSRG_FNO_ERR_ARG;
   if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
   if (!is_device_ptr(dvv) || !is_device_ptr(on_out) || !is_device_ptr(no_out)) return DSRG_FNO_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> lk(workspace_mutex());
-  Workspace& ws = workspace_for_current_device();
   const size_t n2 = (size_t)nvir * nvir;
   DSRG_TRY(ws_reserve(ws, 2 * doubles(n2) + doubles(eig_work_doubles(nvir)) + ws_bytes(nvir + 8, sizeof(int))));
   double* A = ws_take<double>(ws, n2);
@@ -569,33 +523,13 @@ int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double thre
   return DSRG_FNO_OK;
 }
 
-int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold, double degen_ratio,
-                 int32_t* nkept_out, void* stream) {
-  if (nvir <= 0 || !ons || !nkept_out || !is_device_ptr(ons)) return DSRG_FNO_ERR_ARG;
-  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> lk(workspace_mutex());
-  Workspace& ws = workspace_for_current_device();
-  DSRG_TRY(ws_reserve(ws, ws_bytes(8, sizeof(int))));
-  int* nk = ws_take<int>(ws, 8);
-  DSRG_TRY(truncate_ons(nvir, ons, mode, threshold, degen_ratio, nk, st));
-  int h = 0;
-  DSRG_CUDA(cudaMemcpyAsync(&h, nk, sizeof(int), cudaMemcpyDeviceToHost, st));
-  DSRG_CUDA(cudaStreamSynchronize(st));
-  *nkept_out = h;
-  return DSRG_FNO_OK;
-}
-
-int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, const double* no,
-                                  const double* e2_mo_in, double* de_out, double* e2_fno_out,
-                                  double* eps_fno_out, void* stream) {
+int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, int32_t nkept,
+                           const double* no, const double* e2_mo_in, double* de_out, double* e2_fno_out,
+                           double* eps_fno_out, cudaStream_t st) {
   int s = validate(prob);
   if (s) return s;
   if (!de_out || !no || nkept < 0 || nkept > prob->nvir || !is_device_ptr(no)) return DSRG_FNO_ERR_ARG;
   if (eps_fno_out && !is_device_ptr(eps_fno_out)) return DSRG_FNO_ERR_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  std::lock_guard<std::mutex> lk(workspace_mutex());
-  Workspace& ws = workspace_for_current_device();
   const Geometry g = geometry_of(prob);
   Geometry gf = g;
   gf.nv = nkept;
@@ -607,7 +541,6 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
                  ws_bytes(nk + 8, sizeof(int)) + doubles((size_t)rows * gf.np + 1) + doubles(g.nh + nk + 1) +
                  doubles(nk + 1);
   const int ks = slices_of(prob);
-  const size_t budget = device_budget() + ws.cap / 2;
   size_t pass_mo = e2_mo_in ? 0 : energy_pass_bytes(g, ks, budget);
   size_t pass_f = nk > 0 ? energy_pass_bytes(gf, ks, budget) : 0;
   const int kpv = pad64(nv);
@@ -676,6 +609,89 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
   *de_out = e_mo - e_f;
   if (e2_fno_out) *e2_fno_out = e_f;
   return DSRG_FNO_OK;
+}
+
+}  // namespace dsrg
+
+using namespace dsrg;
+
+extern "C" {
+
+const char* dsrg_fno_status_string(int s) {
+  switch (s) {
+    case DSRG_FNO_OK: return "ok";
+    case DSRG_FNO_ERR_ARG: return "invalid argument";
+    case DSRG_FNO_ERR_CUDA: return "CUDA runtime error";
+    case DSRG_FNO_ERR_NOMEM: return "device workspace allocation failed";
+    case DSRG_FNO_ERR_NOCONV: return "eigensolver did not converge";
+    case DSRG_FNO_ERR_TIMEOUT: return "bounded device wait expired";
+    case DSRG_FNO_ERR_NONFINITE: return "non-finite input or result";
+    case DSRG_FNO_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+void dsrg_fno_release(void) {
+  release_batch_pools();
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < 64; ++d) {
+    if (g_ws[d].base) {
+      cudaSetDevice(d);
+      cudaDeviceSynchronize();
+      cudaFree(g_ws[d].base);
+      g_ws[d].base = nullptr;
+      g_ws[d].cap = 0;
+      g_ws[d].off = 0;
+    }
+  }
+  cudaSetDevice(cur);
+}
+
+int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stream) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  return impl_pt2_energy(ws, device_budget() + ws.cap / 2, prob, e2_out, (cudaStream_t)stream);
+}
+
+int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out, void* stream) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  return impl_vv_opdm(ws, device_budget() + ws.cap / 2, prob, dvv_out, e2_out, (cudaStream_t)stream);
+}
+
+int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,
+                      double* on_out, double* no_out, int32_t* nkept_out, void* stream) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  return impl_truncate(ws, nvir, dvv, mode, threshold, degen_ratio, on_out, no_out, nkept_out, (cudaStream_t)stream);
+}
+
+int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold, double degen_ratio,
+                 int32_t* nkept_out, void* stream) {
+  if (nvir <= 0 || !ons || !nkept_out || !is_device_ptr(ons)) return DSRG_FNO_ERR_ARG;
+  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  DSRG_TRY(ws_reserve(ws, ws_bytes(8, sizeof(int))));
+  int* nk = ws_take<int>(ws, 8);
+  DSRG_TRY(truncate_ons(nvir, ons, mode, threshold, degen_ratio, nk, st));
+  int h = 0;
+  DSRG_CUDA(cudaMemcpyAsync(&h, nk, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  *nkept_out = h;
+  return DSRG_FNO_OK;
+}
+
+int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, const double* no,
+                                  const double* e2_mo_in, double* de_out, double* e2_fno_out,
+                                  double* eps_fno_out, void* stream) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  return impl_correction(ws, device_budget() + ws.cap / 2, prob, nkept, no, e2_mo_in, de_out, e2_fno_out, eps_fno_out,
+                         (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -354,8 +354,12 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   DSRG_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
   DSRG_CUDA(cudaMemsetAsync(status_dev, 0, 4 * sizeof(int), st));
   const size_t smem = sizeof(float4) * (size_t)(m / 2);
-  if (smem > 200 * 1024) return DSRG_FNO_ERR_UNSUPPORTED;
-  DSRG_CUDA(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  constexpr int SMEM_CEILING = 200 * 1024;
+  if (smem > (size_t)SMEM_CEILING) return DSRG_FNO_ERR_UNSUPPORTED;
+  // one fixed ceiling for every launch: concurrent callers (batch workers)
+  // never lower it under one another
+  if (smem > 48 * 1024)
+    DSRG_CUDA(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CEILING));
   int dev = 0, sms = 0, occ = 0;
   DSRG_CUDA(cudaGetDevice(&dev));
   DSRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -122,4 +122,18 @@ int scale_rows(int nv, int ncol, long ld, const double* ev, const double* V, dou
 int copy_active(long rows, int na, int np, int npf, const double* B, double* Bf, cudaStream_t st);
 int check_finite(const double* x, long n, int* flag, cudaStream_t st);
 
+// Single-instance pipeline stages on an explicit workspace (abi.cu); the C
+// entry points call them on the per-device workspace, the batch runner on
+// its workers' workspaces.  `budget`: device bytes a pass may plan for.
+size_t device_budget();
+void release_batch_pools();  // batch.cu
+int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* e2_out, cudaStream_t st);
+int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
+                 cudaStream_t st);
+int impl_truncate(Workspace& ws, int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,
+                  double* on_out, double* no_out, int32_t* nkept_out, cudaStream_t st);
+int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, int32_t nkept, const double* no,
+                    const double* e2_mo_in, double* de_out, double* e2_fno_out, double* eps_fno_out,
+                    cudaStream_t st);
+
 }  // namespace dsrg

@@ -589,14 +589,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  // initialised once, thread-safe (function-local static)
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -615,14 +616,10 @@ int make_plane_map(CUtensorMap* map, const void* planes, int KS, long rows, int 
 }
 
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
 }
 
 template <int KS, int BN, int STAGES>
@@ -633,11 +630,8 @@ int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kp
   DSRG_TRY(make_plane_map(&ma, pa, KS, rows_a, Kpad, BM));
   DSRG_TRY(make_plane_map(&mb, pb, KS, rows_b, Kpad, BN));
   auto kern = sliced_gemm_kernel<KS, BN, STAGES>;
-  static bool attr = false;
-  if (!attr) {
-    DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    attr = true;
-  }
+  // the same value on every launch (per device, idempotent, thread-safe)
+  DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   if (P.njobs <= 0) return DSRG_FNO_OK;
   const int grid = std::min(P.njobs, num_sms());
   void* tok = nullptr;

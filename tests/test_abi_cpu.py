@@ -16,7 +16,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", h)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"^\s*(?:int|void|int64_t|const char\s*\*)\s*(dsrg_fno_\w+)\s*\(", text, flags=re.M)
+        names += re.findall(r"^\s*(?:int|void|int32_t|int64_t|const char\s*\*)\s*(dsrg_fno_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
