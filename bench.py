@@ -23,12 +23,19 @@ import subprocess
 import sys
 import threading
 import time
+import types
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 DEFAULT_WORKLOAD = "sa_cas10_ncore60_nvir1200_naux3600"
+# 64 independent instances of ragged size (synth.problems.batch_sizes, seed 3)
+BATCH_WORKLOAD = "ragged_batch64_seed3"
+BATCH_CUT = 98.5
+PHASES = ("sliced_gemm_pair", "sliced_gemm_syrk", "sliced_gemm_plain", "phase_stage_b", "phase_pair_epilogue",
+          "phase_dress", "phase_stage_sig", "phase_small_terms", "phase_no_eigen", "phase_density_eigen",
+          "phase_recanon_and_rotate")
 METRIC = "DSRG-PT2 D_vv+E2 solves/sec & GFLOP/s, fast vs FP64 GPU form at ≤1e-7 Eh"
 
 
@@ -147,25 +154,47 @@ def cpu_baseline(p, seconds):
                       f"{frac:.3e} of a solve's algorithmic flops, scaled"}
 
 
+def batch_cpu_baseline(seconds):
+    """The oracle on the largest instance of the ragged batch, as in
+    cpu_baseline, rescaled from that instance's flops to the batch's
+    (instances per second of the whole 64-instance mix)."""
+    from synth.problems import batch_sizes, batch_problem
+    sizes = batch_sizes()
+    fl = [algorithmic_flops(types.SimpleNamespace(**s)) for s in sizes]
+    k = max(range(len(sizes)), key=lambda i: fl[i])
+    r = cpu_baseline(batch_problem(k), seconds)
+    flops_per_s = r["value"] * fl[k]
+    r["value"] = flops_per_s / (sum(fl) / len(fl))
+    r["unit"] = "instances/s"
+    r["sample"] = f"instance {k} of the batch (largest): " + r["sample"] + "; rescaled by the batch's mean flops"
+    return r
+
+
 def reference_arm(args):
     from synth import workload
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p = workload(args.workload)
+    batch = args.workload == BATCH_WORKLOAD
+    if batch:
+        base = lambda sec: batch_cpu_baseline(sec)  # noqa: E731
+    else:
+        p = workload(args.workload)
+        base = lambda sec: cpu_baseline(p, sec)  # noqa: E731
     vals = []
     for _ in range(args.warmup):
-        cpu_baseline(p, max(2.0, args.cpu_seconds / 4))
+        base(max(2.0, args.cpu_seconds / 4))
     for _ in range(args.steps):
-        vals.append(cpu_baseline(p, args.cpu_seconds))
+        vals.append(base(args.cpu_seconds))
     v = sum(x["value"] for x in vals) / len(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+    unit = vals[0]["unit"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": vals[0]["cores"], "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": unit, "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
-            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -174,6 +203,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == BATCH_WORKLOAD:
+        batch_arm(args)
         return
     import numpy as np
     import torch
@@ -237,9 +269,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clocks = clk.stop()
     phases = {}
-    for nm in ("sliced_gemm_pair", "sliced_gemm_syrk", "sliced_gemm_plain", "phase_stage_b", "phase_pair_epilogue",
-               "phase_dress", "phase_stage_sig", "phase_small_terms", "phase_no_eigen", "phase_density_eigen",
-               "phase_recanon_and_rotate"):
+    for nm in PHASES:
         t_ms, n_l, _ = pkg.dsrg_fno_profile_query(nm)
         phases[nm] = {"ms_per_step": t_ms / args.steps, "launches_or_calls": n_l}
     pair_ms, pair_n, pair_fl = pkg.dsrg_fno_profile_query("sliced_gemm_pair")
@@ -302,19 +332,7 @@ def main():
                                     **{f"de_{c}": res[c][1] - r64[c][1] for c in cuts},
                                     **{f"nkept_{c}": [res[c][0], r64[c][0]] for c in cuts}}}
 
-    peaks, peak_kind = measured_peaks()
-    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    achieved = (pair_fl / (pair_ms / 1e3) / 1e12) if pair_ms > 0 else None
-    roofline = {"bound": "tensor", "kernel": "sliced_gemm_kernel (pair contraction, tcgen05 bf16 digit planes)",
-                "achieved": achieved, "peak": peak, "peak_kind": f"bf16 dense sustained, {peak_kind}",
-                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "launches": pair_n, "avg_launch_ms": pair_ms / max(pair_n, 1),
-                "executed_flops_per_launch": pair_fl / max(pair_n, 1),
-                "share_of_step": pair_ms / ms if ms > 0 else None,
-                "syrk": {"ms": syrk_ms, "launches": syrk_n,
-                         "tflops": (syrk_fl / (syrk_ms / 1e3) / 1e12) if syrk_ms > 0 else None},
-                "plain": {"ms": plain_ms, "launches": plain_n,
-                          "tflops": (plain_fl / (plain_ms / 1e3) / 1e12) if plain_ms > 0 else None}}
+    roofline = roofline_of(pair_ms, pair_n, pair_fl, (syrk_ms, syrk_n, syrk_fl), (plain_ms, plain_n, plain_fl), ms)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -335,6 +353,179 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def roofline_of(pair_ms, pair_n, pair_fl, syrk, plain, step_ms):
+    peaks, peak_kind = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    achieved = (pair_fl / (pair_ms / 1e3) / 1e12) if pair_ms > 0 else None
+    tf = lambda q: (q[2] / (q[0] / 1e3) / 1e12) if q[0] > 0 else None  # noqa: E731
+    return {"bound": "tensor", "kernel": "sliced_gemm_kernel (pair contraction, tcgen05 bf16 digit planes)",
+            "achieved": achieved, "peak": peak, "peak_kind": f"bf16 dense sustained, {peak_kind}",
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "launches": pair_n, "avg_launch_ms": pair_ms / max(pair_n, 1),
+            "executed_flops_per_launch": pair_fl / max(pair_n, 1),
+            "share_of_step": pair_ms / step_ms if step_ms > 0 else None,
+            "syrk": {"ms": syrk[0], "launches": syrk[1], "tflops": tf(syrk)},
+            "plain": {"ms": plain[0], "launches": plain[1], "tflops": tf(plain)}}
+
+
+def batch_arm(args):
+    """64 ragged instances per step through dsrg_fno_batch_run (autotuned
+    worker count): E_vv, D_vv, NOs, the p_o cut and the correction of each."""
+    import numpy as np
+    import torch
+
+    import paper_2312_07008_gb300 as pkg
+    from synth.problems import batch_sizes, batch_problem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    dev = torch.device("cuda", local)
+    sizes = batch_sizes()
+    probs = [batch_problem(k) for k in range(len(sizes))]
+    n = len(probs)
+    gps = [pkg.problem_from_synth(p, dev, pkg.SLICED_BF16, args.nslices) for p in probs]
+    dvv = [torch.empty((p.nvir, p.nvir), dtype=torch.float64, device=dev) for p in probs]
+    on = [torch.empty(p.nvir, dtype=torch.float64, device=dev) for p in probs]
+    no = [torch.empty((p.nvir, p.nvir), dtype=torch.float64, device=dev) for p in probs]
+    cut = (pkg.MODE_PO, BATCH_CUT, 0.01)
+
+    def step(items):
+        return pkg.dsrg_fno_batch_run(items, dvv, cut, on, no, correction=True, nworkers=0)
+
+    for _ in range(args.warmup):
+        step(gps)
+    workers = pkg.dsrg_fno_batch_last_workers()
+    stream = torch.cuda.current_stream()
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    pkg.dsrg_fno_launch_count(reset=True)
+    pkg.dsrg_fno_profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        res = step(gps)
+    ev1.record(stream)
+    barrier()
+    pkg.dsrg_fno_profile_enable(False)
+    launches = pkg.dsrg_fno_launch_count()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.stop()
+    q = {nm: pkg.dsrg_fno_profile_query(nm) for nm in ("sliced_gemm_pair", "sliced_gemm_syrk", "sliced_gemm_plain")}
+    # stream time per step summed over the concurrent workers
+    phases = {}
+    for nm in PHASES:
+        t_ms, n_l, _ = pkg.dsrg_fno_profile_query(nm)
+        phases[nm] = {"stream_ms_per_step": t_ms / args.steps, "launches_or_calls": n_l}
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = args.steps * world * n / (ms_max / 1e3)
+    flops = sum(algorithmic_flops(p) for p in probs)
+
+    # ---- end to end: every instance's inputs from pinned host memory each step
+    host, dbufs, gp_e2e = [], [], []
+    for p in probs:
+        h = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+             for k, v in (("B", p.B), ("eps", p.eps), ("g1", p.gamma1), ("l2", p.lambda2)) if v is not None}
+        db = {k: torch.empty_like(v, device=dev) for k, v in h.items()}
+        host.append(h)
+        dbufs.append(db)
+        gp_e2e.append(pkg.Problem(p.ncore, p.nact, p.nvir, p.naux, db["B"], db["eps"], db.get("g1"), db.get("l2"),
+                                  None, p.weights, p.s, pkg.SLICED_BF16, args.nslices))
+    h2d = sum(v.numel() * v.element_size() for h in host for v in h.values())
+    on_host = [torch.empty(p.nvir, dtype=torch.float64).pin_memory() for p in probs]
+    d2h = sum(x.numel() * 8 for x in on_host) + n * 8 * 3
+
+    def e2e_step():
+        for h, db in zip(host, dbufs):
+            for k in h:
+                db[k].copy_(h[k], non_blocking=True)
+        r = step(gp_e2e)
+        for a, b in zip(on_host, on):
+            a.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+        return r
+
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = args.steps * world * n / (float(te.item()) / 1e3)
+
+    # ---- the float64 GPU form on every 4th instance (a 16-instance sample)
+    fp64 = None
+    if args.fp64_steps > 0:
+        idx = list(range(0, n, 4))
+        g64 = [pkg.problem_from_synth(probs[i], dev, pkg.FP64) for i in idx]
+        sub = lambda xs: [xs[i] for i in idx]  # noqa: E731
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        f0.record(stream)
+        r64 = pkg.dsrg_fno_batch_run(g64, sub(dvv), cut, sub(on), sub(no), correction=True, nworkers=0)
+        f1.record(stream)
+        barrier()
+        fms = f0.elapsed_time(f1)
+        rf = pkg.dsrg_fno_batch_run(sub(gps), sub(dvv), cut, sub(on), sub(no), correction=True, nworkers=workers)
+        fl64 = sum(algorithmic_flops(probs[i]) for i in idx)
+        fp64 = {"sample": "every 4th instance (16)", "instances_per_s": len(idx) / (fms / 1e3),
+                "gflops": fl64 / (fms / 1e3) / 1e9,
+                "fast_minus_fp64": {"max_abs_e2": max(abs(a["e2"] - b["e2"]) for a, b in zip(rf, r64)),
+                                    "max_abs_de": max(abs(a["de"] - b["de"]) for a, b in zip(rf, r64)),
+                                    "nkept_equal": all(a["nkept"] == b["nkept"] for a, b in zip(rf, r64))}}
+
+    roofline = roofline_of(*q["sliced_gemm_pair"], q["sliced_gemm_syrk"], q["sliced_gemm_plain"], ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": f"bf16 digit planes (k={args.nslices}) -> exact f32 level sums -> f64",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "instances": n, "ncore": "U{10..60}", "nact": "{0,4,6,8}",
+                   "nvir": "U{100..800}", "naux": "3 (ncore+nact+nvir)", "nstates": "2..5",
+                   "cut_po": BATCH_CUT, "nslices": args.nslices, "workers": workers,
+                   "l2": f"inputs larger than L2 ({sum(p.B.nbytes for p in probs) / 1e9:.1f} GB of B)",
+                   "parallelism": "replicas"},
+        "gflops": flops * value / n / 1e9,
+        "s_per_step": ms_max / args.steps / 1e3,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "instances/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "phases": phases,
+        "clocks": clocks,
+        "fp64_form": fp64,
+        "result": {"sum_e2": sum(r["e2"] for r in res), "sum_nkept": sum(r["nkept"] for r in res),
+                   "sum_de": sum(r["de"] for r in res)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batch_cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

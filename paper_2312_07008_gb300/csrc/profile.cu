@@ -17,6 +17,10 @@ struct ProfRec {
   double flops;
 };
 static std::vector<ProfRec> g_recs;
+// Event pairs are kept across profiling sessions: creating events while
+// other threads launch work contends on the driver, so a session reuses the
+// pairs of earlier ones and creates only what it lacks.
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_event_pool;
 static std::mutex g_prof_mutex;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -30,8 +34,14 @@ void prof_begin(const char* name, double flops, cudaStream_t st, void** token) {
   ProfRec r;
   r.name = name;
   r.flops = flops;
-  cudaEventCreate(&r.a);
-  cudaEventCreate(&r.b);
+  if (g_recs.size() < g_event_pool.size()) {
+    r.a = g_event_pool[g_recs.size()].first;
+    r.b = g_event_pool[g_recs.size()].second;
+  } else {
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    g_event_pool.emplace_back(r.a, r.b);
+  }
   cudaEventRecord(r.a, st);
   g_recs.push_back(r);
   *token = reinterpret_cast<void*>(g_recs.size());
@@ -51,10 +61,9 @@ using namespace dsrg;
 extern "C" void dsrg_fno_profile_enable(int32_t enable) {
   std::lock_guard<std::mutex> lk(g_prof_mutex);
   if (enable) {
-    for (auto& r : g_recs) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
-    }
+    // the pairs of the last session go back to the pool; wait until they
+    // have been reached so that re-recording them is safe
+    for (auto& r : g_recs) cudaEventSynchronize(r.b);
     g_recs.clear();
   }
   g_prof = enable != 0;

@@ -37,8 +37,9 @@ namespace dsrg {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BKE = 64;            // k elements per block (128 bytes of bf16)
-constexpr int KCHUNK_BLOCKS = 5;   // 320 k-values per exact sum of levels 0, 1, 2
+constexpr int BKE = 64;            // k elements per block (128 bytes of bf16, 128-byte swizzle)
+constexpr int ROW_BYTES = 2 * BKE;
+constexpr int KCHUNK_BLOCKS = 320 / BKE;  // 320 k-values per exact sum of levels 0, 1, 2
 constexpr int NEXACT = 3;          // levels kept exact per chunk
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
 
@@ -270,12 +271,15 @@ __device__ __forceinline__ void seg_range(const GemmParams& P, int split, int* r
 
 template <int KS, int BN, int STAGES>
 struct Cfg {
-  static constexpr int A_SLICE = BM * 128;
-  static constexpr int B_SLICE = BN * 128;
+  static constexpr int A_SLICE = BM * ROW_BYTES;
+  static constexpr int B_SLICE = BN * ROW_BYTES;
+  static_assert(A_SLICE % 1024 == 0 && B_SLICE % 1024 == 0, "plane tiles keep the 1024-byte swizzle atoms aligned");
   static constexpr int A_BYTES = KS * A_SLICE;
   static constexpr int B_BYTES = KS * B_SLICE;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static_assert(SMEM <= 232448, "dynamic shared memory per block");
+  static_assert((2 * STAGES + 9) * 8 + 8 <= 256, "barrier area");
   static constexpr int TMEM_COLS = 512;
   static constexpr int SET_COLS = NEXACT * BN;              // exact levels of one chunk
   static constexpr int TAIL_BASE = 2 * SET_COLS;             // lower levels of one segment
@@ -408,6 +412,8 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             tc::tc_fence_after();
             const uint32_t a_base = tc::smem_u32(smem + s * C::STAGE_BYTES);
             const uint32_t b_base = a_base + C::A_BYTES;
+            const uint64_t a_desc0 = tc::make_sdesc_sw128(a_base);
+            const uint64_t b_desc0 = tc::make_sdesc_sw128(b_base);
 #pragma unroll
             for (int sa = 0; sa < KS; ++sa) {
 #pragma unroll
@@ -421,8 +427,9 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
                 const bool first_block = exact ? (kc == 0) : (kb == 0);
 #pragma unroll
                 for (int kk = 0; kk < BKE / 16; ++kk) {
-                  const uint64_t ad = tc::make_sdesc_sw128(a_base + sa * C::A_SLICE + kk * 32);
-                  const uint64_t bd = tc::make_sdesc_sw128(b_base + sb * C::B_SLICE + kk * 32);
+                  // start-address field += byte offset / 16 (no carry: shared addresses < 2^18)
+                  const uint64_t ad = a_desc0 + (uint64_t)((sa * C::A_SLICE + kk * 32) >> 4);
+                  const uint64_t bd = b_desc0 + (uint64_t)((sb * C::B_SLICE + kk * 32) >> 4);
                   const uint32_t acc = (first_block && kk == 0 && sa == 0) ? 0u : 1u;
                   tc::mma_bf16(d, ad, bd, IDESC, acc);
                 }
@@ -601,7 +608,7 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D map over planes [KS][rows][Kpad] bf16, box {64, box_rows, KS}, 128B swizzle.
+// 3-D map over planes [KS][rows][Kpad] bf16, box {BKE, box_rows, KS}, 128-byte swizzle.
 int make_plane_map(CUtensorMap* map, const void* planes, int KS, long rows, int Kpad, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return DSRG_FNO_ERR_CUDA;
