@@ -190,8 +190,9 @@ struct PassBuffers {
   int kpad_q, kpad_v; // padded contraction lengths (naux, nvir)
   __nv_bfloat16 *planes_b, *planes_s;
   int *exps_b, *exps_s, *err;
-  float2* nu;      // double-float contraction tiles
-  float2* eps_dd;  // orbital energies as double-float
+  float2* nu;        // double-float contraction tiles
+  float2* eps_dd;    // orbital energies as double-float
+  unsigned* rowmax;  // max |hi| per row of the dressed matrices (float bits)
 };
 
 // In the fast form tau, kappa and the dressed matrices are double-float
@@ -267,12 +268,15 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
     }
     {
       DSRG_PHASE("phase_dress", st);
-      if (W.ks)
+      if (W.ks) {
+        unsigned* rm = want_d ? W.rowmax : nullptr;
+        if (rm) DSRG_CUDA(cudaMemsetAsync(rm, 0, sizeof(unsigned) * (size_t)b.nout * g.nv, st));
         DSRG_TRY(dress_dd(g, W.desc + b.desc_begin, b.ndesc, b.ncc, aux, as_dd(W.tau), as_dd(W.kap), as_dd(W.sig),
-                          W.sig_sign, W.e_part, want_d, st));
-      else
+                          W.sig_sign, W.e_part, want_d, rm, st));
+      } else {
         DSRG_TRY(dress_f64(g, W.desc + b.desc_begin, b.ndesc, b.ncc, aux, W.tau, W.kap, W.sig, W.sig_sign,
                            W.e_part, want_d, st));
+      }
     }
     DSRG_TRY(ordered_sum(W.e_part, (long)b.ndesc * DRESS_TILE_BLOCKS, W.e_acc, bi > 0, st));
     if (want_d) {
@@ -280,7 +284,8 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
         const long rows = (long)b.nout * g.nv;
         {
           DSRG_PHASE("phase_stage_sig", st);
-          DSRG_TRY(slice_rows_dd(W.ks, as_dd(W.sig), rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, st));
+          DSRG_TRY(slice_rows_dd(W.ks, as_dd(W.sig), rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, W.rowmax,
+                                 st));
         }
         DSRG_TRY(sliced_syrk(W.ks, g.nv, b.nout, W.planes_s, W.exps_s, W.kpad_v, W.sig_sign, W.dpart, W.nsplit, D,
                              W.err, st));
@@ -326,7 +331,7 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
     b += doubles((size_t)P.max_pairs * g.np * g.np);
     b += doubles((size_t)g.nh + g.nv);
     if (want_d)
-      b += ws_bytes((size_t)ks * P.max_out * g.nv * pad64(g.nv), 2) + ws_bytes((size_t)P.max_out * g.nv, sizeof(int));
+      b += ws_bytes((size_t)ks * P.max_out * g.nv * pad64(g.nv), 2) + 2 * ws_bytes((size_t)P.max_out * g.nv, sizeof(int));
     b += ws_bytes(8, sizeof(int));
   }
   return b;
@@ -372,6 +377,7 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
     if (want_d) {
       W.planes_s = ws_take<__nv_bfloat16>(ws, (size_t)ks * P.max_out * g.nv * W.kpad_v);
       W.exps_s = ws_take<int>(ws, (size_t)P.max_out * g.nv);
+      W.rowmax = ws_take<unsigned>(ws, (size_t)P.max_out * g.nv);
     }
     W.err = ws_take<int>(ws, 8);
     if (!W.err) return DSRG_FNO_ERR_NOMEM;

@@ -29,16 +29,26 @@ struct RegTables {
   dd log2e, ln2, sixth;
 };
 
-__device__ void reg_tables_init(RegTables& R) {
+// Filled once per device (float64 exp2 / expm1, then split); kernels copy it
+// to shared memory.
+__device__ RegTables g_reg;
+
+__global__ void reg_tables_fill_kernel() {
   for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-    R.T[j] = dd_from_double(exp2(-j / 64.0));
-    R.C[j] = dd_from_double(-expm1(-j * 0.69314718055994530942 / 64.0));
+    g_reg.T[j] = dd_from_double(exp2(-j / 64.0));
+    g_reg.C[j] = dd_from_double(-expm1(-j * 0.69314718055994530942 / 64.0));
   }
   if (threadIdx.x == 0) {
-    R.log2e = dd_from_double(1.44269504088896340736);
-    R.ln2 = dd_from_double(0.69314718055994530942);
-    R.sixth = dd_from_double(1.0 / 6.0);
+    g_reg.log2e = dd_from_double(1.44269504088896340736);
+    g_reg.ln2 = dd_from_double(0.69314718055994530942);
+    g_reg.sixth = dd_from_double(1.0 / 6.0);
   }
+}
+
+__device__ __forceinline__ void reg_tables_load(RegTables& R) {
+  const float* src = reinterpret_cast<const float*>(&g_reg);
+  float* dst = reinterpret_cast<float*>(&R);
+  for (int k = threadIdx.x; k < (int)(sizeof(RegTables) / sizeof(float)); k += blockDim.x) dst[k] = src[k];
 }
 
 // R1 = (1 - exp(-s Delta^2)) / Delta and y = exp(-s Delta^2), double-float.
@@ -79,8 +89,6 @@ __device__ __forceinline__ void regularize(dd delta, dd s, const RegTables& R, d
   *r1 = dd_div(omy, delta);
 }
 
-// tau / kappa (vv, double-float) and t^{ij}_{ex} (va / av, float64) from the
-// double-float contraction tiles nu[slot][a][b].  One block per (row a, slot).
 __global__ void eps_dd_kernel(int n, const double* __restrict__ eps, float2* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) {
@@ -89,6 +97,11 @@ __global__ void eps_dd_kernel(int n, const double* __restrict__ eps, float2* __r
   }
 }
 
+constexpr int EPI_ROWS = 8;  // rows a of one pair per block
+
+// tau / kappa (vv, double-float) and t^{ij}_{ex} (va / av, float64) from the
+// double-float contraction tiles nu[slot][a][b].  One block per EPI_ROWS rows
+// of one pair.
 __global__ void __launch_bounds__(256) pair_epilogue_dd_kernel(Geometry g, const double* __restrict__ eps,
                                                                const float2* __restrict__ eps_dd,
                                                                const int2* __restrict__ pairs,
@@ -96,26 +109,31 @@ __global__ void __launch_bounds__(256) pair_epilogue_dd_kernel(Geometry g, const
                                                                float2* __restrict__ tau, float2* __restrict__ kap,
                                                                double* __restrict__ ts) {
   __shared__ RegTables R;
-  reg_tables_init(R);
-  __syncthreads();
-  const int a = blockIdx.x, slot = blockIdx.y;
+  __shared__ float2 s_ca[EPI_ROWS];
+  reg_tables_load(R);
+  const int a0 = blockIdx.x * EPI_ROWS, slot = blockIdx.y;
   const int na = g.na, nv = g.nv, np = g.np;
-  const bool av = a >= na;
   const int2 pr = pairs[slot];
   const int i = pr.x, j = pr.y;
   const double* ep = eps + g.nc;
-  // Delta = (eps_i + eps_j - eps_a) - eps_b, rounded once to double-float per row
-  const dd ca = dd_from_double(eps[i] + eps[j] - ep[a]);
+  // Delta = (eps_i + eps_j - eps_a) - eps_b, the row part rounded once to double-float
+  if (threadIdx.x < EPI_ROWS && a0 + threadIdx.x < np) {
+    const dd ca = dd_from_double(eps[i] + eps[j] - ep[a0 + threadIdx.x]);
+    s_ca[threadIdx.x] = make_float2(ca.hi, ca.lo);
+  }
+  __syncthreads();
   const dd s = dd_from_double(g.s);
-  const float2* nrow = nu + ((long)slot * np + a) * np;
-  for (int b = threadIdx.x; b < np; b += blockDim.x) {
-    const bool bv = b >= na;
+  const int rows = min(EPI_ROWS, np - a0);
+  for (int idx = threadIdx.x; idx < rows * np; idx += blockDim.x) {
+    const int a = a0 + idx / np, b = idx % np;
+    const bool av = a >= na, bv = b >= na;
     if (!av && !bv) continue;
     if (ts == nullptr && !(av && bv)) continue;
-    const float2 nn = nrow[b];
+    const float2 nn = nu[((long)slot * np + a) * np + b];
     const dd n = {nn.x, nn.y};
     const float2 eb = eps_dd[g.nc + b];
-    const dd delta = dd_sub(ca, dd{eb.x, eb.y});
+    const float2 ca2 = s_ca[a - a0];
+    const dd delta = dd_sub(dd{ca2.x, ca2.y}, dd{eb.x, eb.y});
     dd r1, y;
     regularize(delta, s, R, &r1, &y);
     const dd t = dd_mul(n, r1);
@@ -137,13 +155,23 @@ __device__ __forceinline__ dd ld(const float2* p, long i) {
   return {v.x, v.y};
 }
 
+// acc + c s: the product's high part is added error-free (TwoSum), its low
+// parts and the accumulator's low word in float32; one renormalisation.
+__device__ __forceinline__ dd dd_fma_acc(dd acc, dd c, dd s) {
+  const dd p = two_prod(c.hi, s.hi);
+  const float e = __fmaf_rn(c.hi, s.lo, __fmaf_rn(c.lo, s.hi, p.lo));
+  dd t = two_sum(acc.hi, p.hi);
+  t.lo = __fadd_rn(t.lo, __fadd_rn(acc.lo, e));
+  return quick_two_sum(t.hi, t.lo);
+}
+
 // Double-float form of the group dressing (same structure as dress.cu).
 template <int OCT>
 __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const DressDesc* __restrict__ desc,
                                                        DressAux aux, const float2* __restrict__ tau,
                                                        const float2* __restrict__ kap, float2* __restrict__ sig,
                                                        double* __restrict__ sig_sign, double* __restrict__ e_part,
-                                                       int want_sig) {
+                                                       int want_sig, unsigned* __restrict__ rowmax) {
   constexpr int NS = (OCT == 2) ? 1 : MAXSLOT;
   // float64 coefficients, converted in place to double-float (same size)
   __shared__ union {
@@ -201,15 +229,19 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
       __syncthreads();
       const dd a = inside ? ld(T, (long)e * nv + f) : dd_make(0.0f);
       const dd b = inside ? ld(K, (long)e * nv + f) : dd_make(0.0f);
-      const dd att = {tT[tx][ty].x, tT[tx][ty].y}, btt = {tK[tx][ty].x, tK[tx][ty].y};
+      // c T + c sgn dg T^T = c (T + sgn dg T^T) with sgn = +-1, dg in {0, 1}:
+      // the two signed combinations are formed once per slot
+      const float du = (float)dg[u];
+      const dd att = {du * tT[tx][ty].x, du * tT[tx][ty].y}, btt = {du * tK[tx][ty].x, du * tK[tx][ty].y};
+      const dd tp = dd_add(a, att), tm = dd_sub(a, att);
+      const dd kp = dd_add(b, btt), km = dd_sub(b, btt);
 #pragma unroll
       for (int o = 0; o < OCT; ++o) {
         if (o < oc) {
           const dd c = cf.f[u][o];
-          const float m2 = (float)(sgn[o] * dg[u]);  // +1, -1 or 0
-          const dd c2 = {c.hi * m2, c.lo * m2};
-          at[o] = dd_add(at[o], dd_add(dd_mul(c, a), dd_mul(c2, att)));
-          ak[o] = dd_add(ak[o], dd_add(dd_mul(c, b), dd_mul(c2, btt)));
+          const bool pos = sgn[o] > 0.0;
+          at[o] = dd_fma_acc(at[o], c, pos ? tp : tm);
+          ak[o] = dd_fma_acc(ak[o], c, pos ? kp : km);
         }
       }
       __syncthreads();
@@ -220,14 +252,29 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
         if (inside) part = dd_add(part, dd_mul_f(dd_mul(lamw[o], dd_mul(at[o], ak[o])), w));
         if (want_sig) {
           const dd v = dd_mul(sqd[o], at[o]);
-          float2* S = sig + (long)(D.out + D.o_begin + o) * nv2;
+          const long mat = D.out + D.o_begin + o;
+          float2* S = sig + mat * nv2;
           if (inside) S[(long)e * nv + f] = make_float2(v.hi, v.lo);
+          if (rowmax) {
+            // max |hi| of row e over this tile (16 lanes share ty)
+            float m = inside ? fabsf(v.hi) : 0.0f;
+#pragma unroll
+            for (int w = 8; w > 0; w >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, w));
+            if (tx == 0 && e < nv) atomicMax(rowmax + mat * nv + e, __float_as_uint(m));
+          }
           if (te != tf) {
             sA[ty][tx] = make_float2(v.hi, v.lo);
             __syncthreads();
             const int fr = F0 + ty, ec = E0 + tx;
             const float sg = (float)sgn[o];
-            if (fr < nv && ec < nv) S[(long)fr * nv + ec] = make_float2(sg * sA[tx][ty].x, sg * sA[tx][ty].y);
+            const bool ok = fr < nv && ec < nv;
+            if (ok) S[(long)fr * nv + ec] = make_float2(sg * sA[tx][ty].x, sg * sA[tx][ty].y);
+            if (rowmax) {
+              float m = ok ? fabsf(sA[tx][ty].x) : 0.0f;
+#pragma unroll
+              for (int w = 8; w > 0; w >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, w));
+              if (tx == 0 && fr < nv) atomicMax(rowmax + mat * nv + fr, __float_as_uint(m));
+            }
             __syncthreads();
           }
         }
@@ -250,7 +297,7 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
 // n regulariser values for tests: r1[k] = R1(delta[k]), y[k] = exp(-s delta^2)
 __global__ void regularize_test_kernel(int n, const double* delta, double s, double* r1, double* y) {
   __shared__ RegTables R;
-  reg_tables_init(R);
+  reg_tables_load(R);
   __syncthreads();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     dd a, b;
@@ -269,10 +316,32 @@ int eps_to_dd(int n, const double* eps, float2* out, cudaStream_t st) {
   return DSRG_FNO_OK;
 }
 
+// The regulariser table of the current device, filled on first use.
+static int ensure_reg_tables() {
+  static std::mutex mu;
+  static bool ready[64] = {};
+  int dev = 0;
+  DSRG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return DSRG_FNO_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ready[dev]) {
+    // on a private stream, waited for: later kernels of every stream see it
+    cudaStream_t s0;
+    DSRG_CUDA(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
+    reg_tables_fill_kernel<<<1, 64, 0, s0>>>();
+    DSRG_LAUNCH_CHECK();
+    DSRG_CUDA(cudaStreamSynchronize(s0));
+    DSRG_CUDA(cudaStreamDestroy(s0));
+    ready[dev] = true;
+  }
+  return DSRG_FNO_OK;
+}
+
 int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd, const int2* pairs, int npairs,
                      const float2* nu, float2* tau, float2* kap, double* ts, cudaStream_t st) {
   if (npairs <= 0) return DSRG_FNO_OK;
-  dim3 grid(g.np, npairs);
+  DSRG_TRY(ensure_reg_tables());
+  dim3 grid(ceil_div(g.np, EPI_ROWS), npairs);
   pair_epilogue_dd_kernel<<<grid, 256, 0, st>>>(g, eps, eps_dd, pairs, nu, tau, kap, ts);
   DSRG_LAUNCH_CHECK();
   return DSRG_FNO_OK;
@@ -280,17 +349,18 @@ int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd,
 
 int dress_dd(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, const DressAux& aux,
              const float2* tau, const float2* kap, float2* sig, double* sig_sign, double* e_part, bool want_sig,
-             cudaStream_t st) {
+             unsigned* rowmax, cudaStream_t st) {
   if (ncc > 0) {
     dim3 grid(DRESS_TILE_BLOCKS, ncc);
     dress_dd_kernel<2><<<grid, GNT, 0, st>>>(g.nv, g.na, d_desc, aux, tau, kap, sig, sig_sign, e_part,
-                                             want_sig ? 1 : 0);
+                                             want_sig ? 1 : 0, rowmax);
     DSRG_LAUNCH_CHECK();
   }
   if (ndesc > ncc) {
     dim3 grid(DRESS_TILE_BLOCKS, ndesc - ncc);
     dress_dd_kernel<DRESS_OC><<<grid, GNT, 0, st>>>(g.nv, g.na, d_desc + ncc, aux, tau, kap, sig, sig_sign,
-                                                    e_part + (long)ncc * DRESS_TILE_BLOCKS, want_sig ? 1 : 0);
+                                                    e_part + (long)ncc * DRESS_TILE_BLOCKS, want_sig ? 1 : 0,
+                                                    rowmax);
     DSRG_LAUNCH_CHECK();
   }
   return DSRG_FNO_OK;
@@ -298,6 +368,7 @@ int dress_dd(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, con
 
 int regularize_test(int n, const double* delta, double s, double* r1, double* y, cudaStream_t st) {
   if (n <= 0) return DSRG_FNO_OK;
+  DSRG_TRY(ensure_reg_tables());
   regularize_test_kernel<<<ceil_div(n, 256), 256, 0, st>>>(n, delta, s, r1, y);
   DSRG_LAUNCH_CHECK();
   return DSRG_FNO_OK;

@@ -72,7 +72,7 @@ extern "C" int dsrg_fno_debug_slice_rows_dd(int32_t ks, int32_t R, int32_t K, co
   DSRG_CUDA(cudaMalloc(&p.p, 2L * ks * R * kp));
   DSRG_CUDA(cudaMalloc(&e.p, sizeof(int) * R));
   DSRG_CUDA(cudaMemcpy(d.p, rows, sizeof(float2) * R * K, cudaMemcpyHostToDevice));
-  DSRG_TRY(slice_rows_dd(ks, (float2*)d.p, R, K, K, 1, kp, (__nv_bfloat16*)p.p, (int*)e.p, 0));
+  DSRG_TRY(slice_rows_dd(ks, (float2*)d.p, R, K, K, 1, kp, (__nv_bfloat16*)p.p, (int*)e.p, nullptr, 0));
   DSRG_CUDA(cudaDeviceSynchronize());
   std::vector<__nv_bfloat16> h((size_t)ks * R * kp);
   DSRG_CUDA(cudaMemcpy(h.data(), p.p, h.size() * 2, cudaMemcpyDeviceToHost));

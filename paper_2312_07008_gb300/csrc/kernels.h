@@ -95,17 +95,20 @@ int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const
 // Fast form: exact bf16 digit planes on tcgen05 (sliced.cu)
 int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
                int* exps, cudaStream_t st);
+// rowmax: NULL, or max |hi| per row as float bits (from dress_dd)
 int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
-                  int* exps, cudaStream_t st);
+                  int* exps, const unsigned* rowmax, cudaStream_t st);
 int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
                      const int2* pairs, int npairs, bool energy_only, float2* nu, int* err, cudaStream_t st);
 // double-float elementwise stages (dd_stages.cu)
 int eps_to_dd(int n, const double* eps, float2* out, cudaStream_t st);
 int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd, const int2* pairs, int npairs,
                      const float2* nu, float2* tau, float2* kap, double* ts, cudaStream_t st);
+// rowmax: NULL, or [nout][nv] zeroed words receiving max |hi| of each row of
+// the dressed matrices written (float bits, atomicMax)
 int dress_dd(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, const DressAux& aux,
              const float2* tau, const float2* kap, float2* sig, double* sig_sign, double* e_part, bool want_sig,
-             cudaStream_t st);
+             unsigned* rowmax, cudaStream_t st);
 int regularize_test(int n, const double* delta, double s, double* r1, double* y, cudaStream_t st);
 int sliced_syrk(int KS, int nv, int nr, const __nv_bfloat16* planes, const int* exps, int Kpad,
                 const double* sign, double* dpart, int nsplit, double* D, int* err, cudaStream_t st);

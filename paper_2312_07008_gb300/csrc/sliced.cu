@@ -119,10 +119,12 @@ __device__ __forceinline__ float2 zero_of(float2) { return make_float2(0.f, 0.f)
 // planes[s][row][k] (bf16, k padded to Kpad with zeros), exps[row].
 // Source element (row, k) at src[row * rs + k * ks]; one of rs, ks is 1.
 // T is double (float64 rows) or float2 (double-float rows).
+// rowmax (optional, double-float rows): max |hi| of each row as float bits,
+// gathered by the producer; the first pass over the row is then skipped.
 template <int KS, typename T>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const T* __restrict__ src, long R, int K, long rs,
                                                          long ks, int Kpad, __nv_bfloat16* __restrict__ planes,
-                                                         int* __restrict__ exps) {
+                                                         int* __restrict__ exps, const unsigned* __restrict__ rowmax) {
   __shared__ T tile[32][33];
   __shared__ int s_exp[32];
   const long row0 = (long)blockIdx.x * 32;
@@ -130,7 +132,10 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const T* __restrict__ s
   const bool kfast = (ks == 1);
   const int myrow = threadIdx.x >> 3, part = threadIdx.x & 7;  // 32 rows x 8 parts
   double mx = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 32) {
+  if (rowmax) {
+    if (part == 0 && row0 + myrow < R) mx = (double)__uint_as_float(rowmax[row0 + myrow]);
+  }
+  for (int k0 = 0; k0 < K && !rowmax; k0 += 32) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       int r = kfast ? ty + 8 * i : tx;
@@ -686,13 +691,13 @@ int tile_n_for(int KS) { return KS == 5 ? 48 : 64; }
 // ------------------------------------------------------------ public (lib)
 template <typename T>
 static int slice_rows_t(int KS, const T* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
-                        int* exps, cudaStream_t st) {
+                        int* exps, const unsigned* rowmax, cudaStream_t st) {
   if (R <= 0) return DSRG_FNO_OK;
   const int grid = (int)((R + 31) / 32);
   switch (KS) {
-    case 3: slice_rows_kernel<3, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
-    case 4: slice_rows_kernel<4, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
-    case 5: slice_rows_kernel<5, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps); break;
+    case 3: slice_rows_kernel<3, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps, rowmax); break;
+    case 4: slice_rows_kernel<4, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps, rowmax); break;
+    case 5: slice_rows_kernel<5, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps, rowmax); break;
     default: return DSRG_FNO_ERR_ARG;
   }
   DSRG_LAUNCH_CHECK();
@@ -701,12 +706,12 @@ static int slice_rows_t(int KS, const T* src, long R, int K, long rs, long ks, i
 
 int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
                int* exps, cudaStream_t st) {
-  return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, st);
+  return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, nullptr, st);
 }
 
 int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
-                  int* exps, cudaStream_t st) {
-  return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, st);
+                  int* exps, const unsigned* rowmax, cudaStream_t st) {
+  return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, rowmax, st);
 }
 
 // nu[slot][a][b] for the listed pairs from B planes ([KS][nh*np][Kpad]).
