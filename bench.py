@@ -36,6 +36,7 @@ BATCH_CUT = 98.5
 PHASES = ("sliced_gemm_pair", "sliced_gemm_syrk", "sliced_gemm_plain", "phase_stage_b", "phase_pair_epilogue",
           "phase_dress", "phase_stage_sig", "phase_small_terms", "phase_no_eigen", "phase_density_eigen",
           "phase_recanon_and_rotate")
+COUNTERS = ("eig_sweeps_large", "eig_sweeps_small")
 METRIC = "DSRG-PT2 D_vv+E2 solves/sec & GFLOP/s, fast vs FP64 GPU form at ≤1e-7 Eh"
 
 
@@ -272,6 +273,9 @@ def main():
     for nm in PHASES:
         t_ms, n_l, _ = pkg.dsrg_fno_profile_query(nm)
         phases[nm] = {"ms_per_step": t_ms / args.steps, "launches_or_calls": n_l}
+    for nm in COUNTERS:
+        _, n_c, total = pkg.dsrg_fno_profile_query(nm)
+        phases[nm] = {"calls": n_c, "mean": total / max(n_c, 1)}
     pair_ms, pair_n, pair_fl = pkg.dsrg_fno_profile_query("sliced_gemm_pair")
     syrk_ms, syrk_n, syrk_fl = pkg.dsrg_fno_profile_query("sliced_gemm_syrk")
     plain_ms, plain_n, plain_fl = pkg.dsrg_fno_profile_query("sliced_gemm_plain")

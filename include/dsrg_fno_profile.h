@@ -19,8 +19,11 @@ extern "C" {
 void dsrg_fno_profile_enable(int32_t enable);
 
 /* Totals over the recorded launches of kernel `name` ("sliced_gemm_pair",
- * "sliced_gemm_syrk", "sliced_gemm_plain", "pair_gemm_f64"): summed event
- * time (ms), number of launches, and summed executed flops.  Returns 0. */
+ * "sliced_gemm_syrk", "sliced_gemm_plain", "pair_gemm_f64", or a phase
+ * "phase_*"): summed event time (ms), number of launches, and summed executed
+ * flops.  Counters without timing ("eig_sweeps_large" / "eig_sweeps_small":
+ * Jacobi sweeps of matrices with n >= 256 / n < 256) report calls in
+ * `launches` and the summed count in `flops`.  Returns 0. */
 int dsrg_fno_profile_query(const char* name, double* total_ms, int64_t* launches, double* flops);
 
 /* Number of kernels the library launched since the last reset; `reset`

@@ -35,6 +35,8 @@ void count_launch();
 bool profiling();
 void prof_begin(const char* name, double flops, cudaStream_t st, void** token);
 void prof_end(void* token, cudaStream_t st);
+// A counter without timing (queried like a kernel: launches = calls, flops = summed value).
+void prof_count(const char* name, double value);
 // Scoped timing of a phase of a call (recorded only while profiling).
 struct PhaseTimer {
   void* tok = nullptr;

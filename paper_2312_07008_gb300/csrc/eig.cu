@@ -52,6 +52,7 @@ struct JacobiArgs {
 // false once any block's wait has expired; the kernel then returns.
 __device__ bool grid_barrier(const JacobiArgs& P) {
   __syncthreads();
+  if (gridDim.x == 1) return true;  // one block: the block barrier is the grid barrier
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     volatile unsigned* gen = P.bar + 1;
@@ -147,7 +148,7 @@ __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double*
   *tot = st;
 }
 
-__global__ void __launch_bounds__(JNT) jacobi_coop_kernel(JacobiArgs P) {
+__global__ void __launch_bounds__(JNT, 3) jacobi_coop_kernel(JacobiArgs P) {
   extern __shared__ float4 s_cs[];  // per pair of the round: c (hi, lo), s (hi, lo)
   const int n = P.n, m = P.m, half = m / 2;
   const long n2 = (long)n * n;
@@ -201,6 +202,10 @@ __global__ void __launch_bounds__(JNT) jacobi_coop_kernel(JacobiArgs P) {
       // work units: (row pair of A, column pair) for half row pairs, then
       // (row of V, column pair) for n rows; consecutive units share a row
       const long units = (long)(half + n) * half;
+      const float2* __restrict__ Ar = A;
+      float2* __restrict__ Bw = B;
+      float2* __restrict__ Vw = P.V;
+#pragma unroll 4
       for (long u = blockIdx.x * (long)JNT + threadIdx.x; u < units; u += (long)gridDim.x * JNT) {
         const int it = (int)(u / half), k = (int)(u % half);
         const int j1 = rr_index(k, r, m), j2 = rr_index(m - 1 - k, r, m);
@@ -214,31 +219,31 @@ __global__ void __launch_bounds__(JNT) jacobi_coop_kernel(JacobiArgs P) {
           const float4 rc = s_cs[it];
           const dd cP = {rc.x, rc.y}, sP = {rc.z, rc.w};
           // M = A[{p,q}, {pc,qc}] J_R
-          const dd a_pp = ldd(A, (long)p * n + pc);
-          const dd a_pq = qcr ? ldd(A, (long)p * n + qc) : dd_make(0.f);
+          const dd a_pp = ldd(Ar, (long)p * n + pc);
+          const dd a_pq = qcr ? ldd(Ar, (long)p * n + qc) : dd_make(0.f);
           const dd m_p0 = qcr ? rot_combine(cR, a_pp, sR, a_pq, true) : a_pp;
           const dd m_p1 = qcr ? rot_combine(sR, a_pp, cR, a_pq, false) : dd_make(0.f);
           if (q < n) {
-            const dd a_qp = ldd(A, (long)q * n + pc);
-            const dd a_qq = qcr ? ldd(A, (long)q * n + qc) : dd_make(0.f);
+            const dd a_qp = ldd(Ar, (long)q * n + pc);
+            const dd a_qq = qcr ? ldd(Ar, (long)q * n + qc) : dd_make(0.f);
             const dd m_q0 = qcr ? rot_combine(cR, a_qp, sR, a_qq, true) : a_qp;
             const dd m_q1 = qcr ? rot_combine(sR, a_qp, cR, a_qq, false) : dd_make(0.f);
             // A' = J_P^T M
-            sdd(B, (long)p * n + pc, rot_combine(cP, m_p0, sP, m_q0, true));
-            sdd(B, (long)q * n + pc, rot_combine(sP, m_p0, cP, m_q0, false));
+            sdd(Bw, (long)p * n + pc, rot_combine(cP, m_p0, sP, m_q0, true));
+            sdd(Bw, (long)q * n + pc, rot_combine(sP, m_p0, cP, m_q0, false));
             if (qcr) {
-              sdd(B, (long)p * n + qc, rot_combine(cP, m_p1, sP, m_q1, true));
-              sdd(B, (long)q * n + qc, rot_combine(sP, m_p1, cP, m_q1, false));
+              sdd(Bw, (long)p * n + qc, rot_combine(cP, m_p1, sP, m_q1, true));
+              sdd(Bw, (long)q * n + qc, rot_combine(sP, m_p1, cP, m_q1, false));
             }
           } else {
-            sdd(B, (long)p * n + pc, m_p0);
-            if (qcr) sdd(B, (long)p * n + qc, m_p1);
+            sdd(Bw, (long)p * n + pc, m_p0);
+            if (qcr) sdd(Bw, (long)p * n + qc, m_p1);
           }
         } else if (qcr) {
           const int i = it - half;
-          const dd v0 = ldd(P.V, (long)i * n + pc), v1 = ldd(P.V, (long)i * n + qc);
-          sdd(P.V, (long)i * n + pc, rot_combine(cR, v0, sR, v1, true));
-          sdd(P.V, (long)i * n + qc, rot_combine(sR, v0, cR, v1, false));
+          const dd v0 = ldd(Vw, (long)i * n + pc), v1 = ldd(Vw, (long)i * n + qc);
+          sdd(Vw, (long)i * n + pc, rot_combine(cR, v0, sR, v1, true));
+          sdd(Vw, (long)i * n + qc, rot_combine(sR, v0, cR, v1, false));
         }
       }
       if (!grid_barrier(P)) return;
@@ -367,14 +372,15 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
   // (half + n) * half work units per round; small matrices use few blocks
   const long units = (long)(m / 2 + n) * (m / 2);
-  int nblk = (int)std::min<long>(std::min(sms * std::min(occ, 2), JMAX_BLOCKS), (units + 8 * JNT - 1) / (8 * JNT));
+  int nblk = (int)std::min<long>(std::min(sms * std::min(occ, 3), JMAX_BLOCKS), (units + 8 * JNT - 1) / (8 * JNT));
   nblk = std::max(nblk, 1);
   void* args[] = {&P};
   DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(nblk), dim3(JNT), args, smem, st));
   DSRG_LAUNCH_CHECK();
-  int h[2] = {0, 0};
-  DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int h[3] = {0, 0, 0};
+  DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
   DSRG_CUDA(cudaStreamSynchronize(st));
+  prof_count(n >= 256 ? "eig_sweeps_large" : "eig_sweeps_small", (double)h[2]);
   if (h[1]) return DSRG_FNO_ERR_TIMEOUT;
   return h[0] ? DSRG_FNO_ERR_NOCONV : DSRG_FNO_OK;
 }

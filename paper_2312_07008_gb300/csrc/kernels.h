@@ -88,7 +88,7 @@ struct SmallFast {
   double* cbuf;           // nv * nv
   int* err;
 };
-constexpr int SLICED_MIN_K = 1024;
+constexpr int SLICED_MIN_K = 256;
 int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1,
                     const double* l2, double* D, double* work, const SmallFast& F, cudaStream_t st);
 

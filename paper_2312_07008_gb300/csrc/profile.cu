@@ -16,6 +16,11 @@ struct ProfRec {
   cudaEvent_t a, b;
   double flops;
 };
+struct ProfCount {
+  std::string name;
+  double value;
+};
+static std::vector<ProfCount> g_counts;
 static std::vector<ProfRec> g_recs;
 // Event pairs are kept across profiling sessions: creating events while
 // other threads launch work contends on the driver, so a session reuses the
@@ -47,6 +52,12 @@ void prof_begin(const char* name, double flops, cudaStream_t st, void** token) {
   *token = reinterpret_cast<void*>(g_recs.size());
 }
 
+void prof_count(const char* name, double value) {
+  if (!g_prof) return;
+  std::lock_guard<std::mutex> lk(g_prof_mutex);
+  g_counts.push_back({name, value});
+}
+
 void prof_end(void* token, cudaStream_t st) {
   if (!token) return;
   std::lock_guard<std::mutex> lk(g_prof_mutex);
@@ -65,6 +76,7 @@ extern "C" void dsrg_fno_profile_enable(int32_t enable) {
     // have been reached so that re-recording them is safe
     for (auto& r : g_recs) cudaEventSynchronize(r.b);
     g_recs.clear();
+    g_counts.clear();
   }
   g_prof = enable != 0;
 }
@@ -84,6 +96,11 @@ extern "C" int dsrg_fno_profile_query(const char* name, double* total_ms, int64_
     } else {
       cudaGetLastError();
     }
+  }
+  for (auto& c : g_counts) {
+    if (name && c.name != name) continue;
+    f += c.value;
+    ++n;
   }
   if (total_ms) *total_ms = t;
   if (launches) *launches = n;

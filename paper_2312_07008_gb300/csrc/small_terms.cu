@@ -21,6 +21,13 @@ struct SI {
   const double* t1;
   const double* g1;  // [na][na]
   const double* l2;  // [na]^4
+  // partial contractions shared by the builders (theta_kernel, lambda_kernel):
+  const double* qaa;  // [u][v][e][w] = sum_z t^{uv}_{ez} Theta^w_z
+  const double* pa;   // [m][u][e][x] = sum_y t^{mu}_{ey} Theta^x_y
+  const double* pb;   // [m][u][e][x] = sum_y t^{um}_{ey} Theta^x_y
+  const double* pla;  // [w][e][x][u] = sum_{vy} t^{wv}_{ey} Lambda^{uv}_{xy}
+  const double* plb;  // [w][e][x][u] = sum_{vy} t^{vw}_{ey} Lambda^{uv}_{xy}
+  const double* plc;  // [w][e][y][u] = sum_{vx} t^{vw}_{ex} Lambda^{uv}_{xy}
   __device__ double t(int i, int j, int e, int x) const {
     return ts[(((long)i * nh + j) * nv + e) * na + x];
   }
@@ -48,6 +55,54 @@ __global__ void t1_kernel(SI S, Geometry g, const double* __restrict__ eps, cons
   }
   const double d = eps[i] - eps[S.nc + S.na + e];
   t1[idx] = (f + 0.5 * c) * regularizer(d, g.s);
+}
+
+// qaa / pa / pb: out[p][e][w] = sum_z t(i_p, j_p, e, z) Theta^w_z over the hole
+// pairs p of one family: 0 = (nc+u, nc+v), p = u na + v; 1 = (m, nc+u) and
+// 2 = (nc+u, m), p = m na + u.
+__global__ void theta_kernel(SI S, int family, long npairs, double* __restrict__ out) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int na = S.na, nv = S.nv, nc = S.nc;
+  if (idx >= npairs * nv * na) return;
+  const int w = (int)(idx % na);
+  const int e = (int)((idx / na) % nv);
+  const long p = idx / ((long)na * nv);
+  const int a = (int)(p / na), b = (int)(p % na);
+  int i, j;
+  if (family == 0) {
+    i = nc + a;
+    j = nc + b;
+  } else if (family == 1) {
+    i = a;
+    j = nc + b;
+  } else {
+    i = nc + b;
+    j = a;
+  }
+  double acc = 0.0;
+  for (int z = 0; z < na; ++z) acc = fma(S.t(i, j, e, z), S.Th(w, z), acc);
+  out[idx] = acc;
+}
+
+// pla / plb / plc: out[w][e][x][u] = sum_{v,y} t(., ., e, .) Lambda^{uv}_{..}
+// variant 0: t^{wv}_{ey} L^{uv}_{xy}; 1: t^{vw}_{ey} L^{uv}_{xy}; 2: t^{vw}_{ex} L^{uv}_{xy}
+// (variant 2 indexes its output [w][e][y][u]).
+__global__ void lambda_kernel(SI S, int variant, double* __restrict__ out) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const int na = S.na, nv = S.nv, nc = S.nc;
+  if (idx >= (long)na * nv * na * na) return;
+  const int u = (int)(idx % na);
+  const int q = (int)((idx / na) % na);  // x (variants 0, 1) or y (variant 2)
+  const int e = (int)((idx / ((long)na * na)) % nv);
+  const int w = (int)(idx / ((long)na * na * nv));
+  double acc = 0.0;
+  for (int v = 0; v < na; ++v)
+    for (int r = 0; r < na; ++r) {
+      if (variant == 0) acc = fma(S.t(nc + w, nc + v, e, r), S.L(u, v, q, r), acc);
+      else if (variant == 1) acc = fma(S.t(nc + v, nc + w, e, r), S.L(u, v, q, r), acc);
+      else acc = fma(S.t(nc + v, nc + w, e, r), S.L(u, v, r, q), acc);
+    }
+  out[idx] = acc;
 }
 
 enum TermId {
@@ -109,14 +164,8 @@ __global__ void build_kernel(SI S, int term, int K, double* __restrict__ X, doub
     case T8_B: {  // t^{um}_{ey} tcheck^{vm}_{fx} Gamma^u_v Theta^x_y
       int m, v, xx;
       unflat3(k, na, na, &m, &v, &xx);
-      for (int u = 0; u < na; ++u) {
-        double gu = S.G(u, v);
-        if (gu == 0.0) continue;
-        for (int yy = 0; yy < na; ++yy) {
-          double tt = term == T8_A ? S.t(m, nc + u, e, yy) : S.t(nc + u, m, e, yy);
-          x = fma(tt * gu, S.Th(xx, yy), x);
-        }
-      }
+      const double* P = term == T8_A ? S.pa : S.pb;
+      for (int u = 0; u < na; ++u) x = fma(S.G(u, v), P[(((long)m * na + u) * S.nv + e) * na + xx], x);
       y = term == T8_A ? 2.0 * S.t(m, nc + v, e, xx) - S.t(nc + v, m, e, xx)
                        : 2.0 * S.t(nc + v, m, e, xx) - S.t(m, nc + v, e, xx);
       break;
@@ -145,13 +194,8 @@ __global__ void build_kernel(SI S, int term, int K, double* __restrict__ X, doub
       int xx, yy, w;
       unflat3(k, na, na, &xx, &yy, &w);
       for (int u = 0; u < na; ++u)
-        for (int v = 0; v < na; ++v) {
-          double l = S.L(u, v, xx, yy);
-          if (l == 0.0) continue;
-          double a = 0.0;
-          for (int z = 0; z < na; ++z) a = fma(S.t(nc + u, nc + v, e, z), S.Th(w, z), a);
-          x = fma(a, l, x);
-        }
+        for (int v = 0; v < na; ++v)
+          x = fma(S.qaa[(((long)u * na + v) * S.nv + e) * na + w], S.L(u, v, xx, yy), x);
       y = S.t(nc + xx, nc + yy, e, w);
       break;
     }
@@ -159,15 +203,9 @@ __global__ void build_kernel(SI S, int term, int K, double* __restrict__ X, doub
       int v, yy, w;
       unflat3(k, na, na, &v, &yy, &w);
       for (int u = 0; u < na; ++u) {
-        double gu = S.G(u, v);
-        if (gu == 0.0) continue;
-        for (int xx = 0; xx < na; ++xx) {
-          double gx = S.G(xx, yy);
-          if (gx == 0.0) continue;
-          double a = 0.0;
-          for (int z = 0; z < na; ++z) a = fma(S.t(nc + u, nc + xx, e, z), S.Th(w, z), a);
-          x = fma(a, gu * gx, x);
-        }
+        double a = 0.0;
+        for (int xx = 0; xx < na; ++xx) a = fma(S.G(xx, yy), S.qaa[(((long)u * na + xx) * S.nv + e) * na + w], a);
+        x = fma(S.G(u, v), a, x);
       }
       y = 2.0 * S.t(nc + v, nc + yy, e, w) - S.t(nc + yy, nc + v, e, w);
       break;
@@ -176,15 +214,8 @@ __global__ void build_kernel(SI S, int term, int K, double* __restrict__ X, doub
     case T12_B: {  // -t^{vw}_{ey} t^{zx}_{fu} Gamma^w_z Lambda^{uv}_{xy}
       int z, xx, u;
       unflat3(k, na, na, &z, &xx, &u);
-      for (int w = 0; w < na; ++w) {
-        double gw = S.G(w, z);
-        if (gw == 0.0) continue;
-        for (int v = 0; v < na; ++v)
-          for (int yy = 0; yy < na; ++yy) {
-            double tt = term == T12_A ? S.t(nc + w, nc + v, e, yy) : S.t(nc + v, nc + w, e, yy);
-            x = fma(tt * gw, S.L(u, v, xx, yy), x);
-          }
-      }
+      const double* P = term == T12_A ? S.pla : S.plb;
+      for (int w = 0; w < na; ++w) x = fma(S.G(w, z), P[(((long)w * S.nv + e) * na + xx) * na + u], x);
       y = term == T12_A ? 2.0 * S.t(nc + z, nc + xx, e, u) - S.t(nc + xx, nc + z, e, u)
                         : S.t(nc + z, nc + xx, e, u);
       break;
@@ -192,12 +223,7 @@ __global__ void build_kernel(SI S, int term, int K, double* __restrict__ X, doub
     case T12_C: {  // -t^{vw}_{ex} t^{yz}_{fu} Gamma^w_z Lambda^{uv}_{xy} ; k = (y, z, u)
       int yy, z, u;
       unflat3(k, na, na, &yy, &z, &u);
-      for (int w = 0; w < na; ++w) {
-        double gw = S.G(w, z);
-        if (gw == 0.0) continue;
-        for (int v = 0; v < na; ++v)
-          for (int xx = 0; xx < na; ++xx) x = fma(S.t(nc + v, nc + w, e, xx) * gw, S.L(u, v, xx, yy), x);
-      }
+      for (int w = 0; w < na; ++w) x = fma(S.G(w, z), S.plc[(((long)w * S.nv + e) * na + yy) * na + u], x);
       y = S.t(nc + yy, nc + z, e, u);
       break;
     }
@@ -226,6 +252,11 @@ static void term_shape(int term, int nc, int na, int* K, double* coef) {
   }
 }
 
+// partial contractions: qaa na^3 nv, pa and pb nc na^2 nv each, pla/plb/plc na^3 nv each
+static size_t partials_doubles(int nc, int na, int nv) {
+  return (size_t)nv * na * na * (4 * (size_t)na + 2 * (size_t)nc);
+}
+
 size_t small_terms_work_doubles(int nc, int na, int nv) {
   long kmax = 0;
   for (int t = 0; t < NTERMS; ++t) {
@@ -234,12 +265,12 @@ size_t small_terms_work_doubles(int nc, int na, int nv) {
     term_shape(t, nc, na, &K, &c);
     kmax = K > kmax ? K : kmax;
   }
-  return 2 * (size_t)nv * (size_t)kmax;
+  return 2 * (size_t)nv * (size_t)kmax + partials_doubles(nc, na, nv);
 }
 
 int t1_amplitudes(const Geometry& g, const double* ts, const double* eps, const double* f_hp, const double* g1,
                   double* t1, cudaStream_t st) {
-  SI S{g.nc, g.na, g.nv, g.nh, ts, nullptr, g1, nullptr};
+  SI S{g.nc, g.na, g.nv, g.nh, ts, nullptr, g1, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   long n = (long)g.nh * g.nv;
   if (n == 0) return DSRG_FNO_OK;
   t1_kernel<<<ceil_div(n, 256), 256, 0, st>>>(S, g, eps, f_hp, t1);
@@ -269,7 +300,38 @@ int small_terms_kmax(int nc, int na) {
 // (digit planes of X and Y, exact level sums), the rest in float64.
 int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1, const double* l2,
                     double* D, double* work, const SmallFast& F, cudaStream_t st) {
-  SI S{g.nc, g.na, g.nv, g.nh, ts, t1, g1, l2};
+  SI S{g.nc, g.na, g.nv, g.nh, ts, t1, g1, l2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (g.na > 0) {
+    // partial contractions after the X / Y area of the largest term
+    const int kmax = small_terms_kmax(g.nc, g.na);
+    double* q = work + 2 * (size_t)g.nv * kmax;
+    const long na = g.na, nv = g.nv, nc = g.nc;
+    double* qaa = q;
+    double* pa = qaa + na * na * nv * na;
+    double* pb = pa + nc * na * nv * na;
+    double* pla = pb + nc * na * nv * na;
+    double* plb = pla + na * nv * na * na;
+    double* plc = plb + na * nv * na * na;
+    const long nq = na * na * nv * na, np_ = nc * na * nv * na, nl = na * nv * na * na;
+    theta_kernel<<<ceil_div(nq, 256), 256, 0, st>>>(S, 0, na * na, qaa);
+    DSRG_LAUNCH_CHECK();
+    if (np_ > 0) {
+      theta_kernel<<<ceil_div(np_, 256), 256, 0, st>>>(S, 1, nc * na, pa);
+      DSRG_LAUNCH_CHECK();
+      theta_kernel<<<ceil_div(np_, 256), 256, 0, st>>>(S, 2, nc * na, pb);
+      DSRG_LAUNCH_CHECK();
+    }
+    for (int v = 0; v < 3; ++v) {
+      lambda_kernel<<<ceil_div(nl, 256), 256, 0, st>>>(S, v, v == 0 ? pla : (v == 1 ? plb : plc));
+      DSRG_LAUNCH_CHECK();
+    }
+    S.qaa = qaa;
+    S.pa = pa;
+    S.pb = pb;
+    S.pla = pla;
+    S.plb = plb;
+    S.plc = plc;
+  }
   for (int term = 0; term < NTERMS; ++term) {
     if (g.na == 0 && term != T1_CORE) continue;
     int K;
