@@ -25,7 +25,13 @@ namespace dsrg {
 
 namespace {
 
-constexpr int JNT = 256;                 // threads per block
+#ifndef JACOBI_THREADS
+#define JACOBI_THREADS 256
+#endif
+#ifndef JACOBI_BLOCKS_PER_SM
+#define JACOBI_BLOCKS_PER_SM 3
+#endif
+constexpr int JNT = JACOBI_THREADS;      // threads per block
 constexpr int JMAX_BLOCKS = EIG_MAX_BLOCKS;
 constexpr long long BAR_SPIN_LIMIT = 20000000;  // ~2 s of 100 ns naps
 
@@ -81,11 +87,11 @@ __device__ bool grid_barrier(const JacobiArgs& P) {
   return s_ok != 0;
 }
 
-__device__ __forceinline__ dd ldd(const float2* p, long i) {
+__device__ __forceinline__ dd ldd(const float2* p, int i) {
   const float2 v = __ldcg(p + i);
   return {v.x, v.y};
 }
-__device__ __forceinline__ void sdd(float2* p, long i, dd v) { __stcg(p + i, make_float2(v.hi, v.lo)); }
+__device__ __forceinline__ void sdd(float2* p, int i, dd v) { __stcg(p + i, make_float2(v.hi, v.lo)); }
 
 // c a +- s b with double-float operands.  The sum keeps an absolute error
 // of a few units of 2^-48 max(|c a|, |s b|), which is what the backward
@@ -114,8 +120,8 @@ __device__ __forceinline__ dd dd_rsqrt12(dd x) {
 __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double* tot) {
   __shared__ double s_o[JNT], s_t[JNT];
   double o = 0.0, t = 0.0;
-  const long n2 = (long)P.n * P.n;
-  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+  const int n2 = P.n * P.n;
+  for (int idx = blockIdx.x * JNT + threadIdx.x; idx < n2; idx += gridDim.x * JNT) {
     const float2 v = __ldcg(A + idx);
     const double a = (double)v.x + (double)v.y;
     t += a * a;
@@ -148,8 +154,10 @@ __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double*
   *tot = st;
 }
 
-__global__ void __launch_bounds__(JNT, 3) jacobi_coop_kernel(JacobiArgs P) {
-  extern __shared__ float4 s_cs[];  // per pair of the round: c (hi, lo), s (hi, lo)
+__global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(JacobiArgs P) {
+  // per pair k of the round: c (hi, lo), s (hi, lo), then the pair (p < q)
+  extern __shared__ float4 s_cs[];
+  int2* s_pq = reinterpret_cast<int2*>(s_cs + P.m / 2);
   const int n = P.n, m = P.m, half = m / 2;
   const long n2 = (long)n * n;
   for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
@@ -176,15 +184,15 @@ __global__ void __launch_bounds__(JNT, 3) jacobi_coop_kernel(JacobiArgs P) {
     prev = off;
     if (sweep == P.max_sweeps) break;
     for (int r = 0; r < m - 1; ++r) {
-      // rotation of every pair of this round (each block forms all of them)
+      // pairs and rotations of this round (each block forms all of them)
       for (int k = threadIdx.x; k < half; k += JNT) {
         const int i1 = rr_index(k, r, m), i2 = rr_index(m - 1 - k, r, m);
         const int p = min(i1, i2), q = max(i1, i2);
         float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
         if (q < n) {
-          const dd apq = dd_mul_f(dd_add(ldd(A, (long)p * n + q), ldd(A, (long)q * n + p)), 0.5f);
+          const dd apq = dd_mul_f(dd_add(ldd(A, p * n + q), ldd(A, q * n + p)), 0.5f);
           if (apq.hi != 0.0f) {
-            const dd d = dd_sub(ldd(A, (long)q * n + q), ldd(A, (long)p * n + p));
+            const dd d = dd_sub(ldd(A, q * n + q), ldd(A, p * n + p));
             const float th = d.hi / (2.0f * apq.hi);
             const float t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
             dd c = dd_rsqrt12(dd_add_f(two_prod(t, t), 1.0f));
@@ -197,53 +205,59 @@ __global__ void __launch_bounds__(JNT, 3) jacobi_coop_kernel(JacobiArgs P) {
           }
         }
         s_cs[k] = cs;
+        s_pq[k] = make_int2(p, q);
       }
       __syncthreads();
-      // work units: (row pair of A, column pair) for half row pairs, then
-      // (row of V, column pair) for n rows; consecutive units share a row
-      const long units = (long)(half + n) * half;
+      // warp tasks: (item, 32 column pairs); items are the half row pairs of
+      // A, then the n rows of V; lane = column pair within the task
+      const int nchunks = (half + 31) >> 5;
+      const int ntasks = (half + n) * nchunks;
       const float2* __restrict__ Ar = A;
       float2* __restrict__ Bw = B;
       float2* __restrict__ Vw = P.V;
-#pragma unroll 4
-      for (long u = blockIdx.x * (long)JNT + threadIdx.x; u < units; u += (long)gridDim.x * JNT) {
-        const int it = (int)(u / half), k = (int)(u % half);
-        const int j1 = rr_index(k, r, m), j2 = rr_index(m - 1 - k, r, m);
-        const int pc = min(j1, j2), qc = max(j1, j2);
+      const int lane = threadIdx.x & 31;
+      const int nwarps = gridDim.x * (JNT / 32);
+#pragma unroll 2
+      for (int task = blockIdx.x * (JNT / 32) + (threadIdx.x >> 5); task < ntasks; task += nwarps) {
+        const int it = task / nchunks;
+        const int k = (task - it * nchunks) * 32 + lane;
+        if (k >= half) continue;
+        const int2 pqc = s_pq[k];
+        const int pc = pqc.x, qc = pqc.y;
         const bool qcr = qc < n;
         const float4 cc = s_cs[k];
         const dd cR = {cc.x, cc.y}, sR = {cc.z, cc.w};
         if (it < half) {
-          const int i1 = rr_index(it, r, m), i2 = rr_index(m - 1 - it, r, m);
-          const int p = min(i1, i2), q = max(i1, i2);
+          const int2 pq = s_pq[it];
+          const int p = pq.x, q = pq.y;
           const float4 rc = s_cs[it];
           const dd cP = {rc.x, rc.y}, sP = {rc.z, rc.w};
           // M = A[{p,q}, {pc,qc}] J_R
-          const dd a_pp = ldd(Ar, (long)p * n + pc);
-          const dd a_pq = qcr ? ldd(Ar, (long)p * n + qc) : dd_make(0.f);
+          const dd a_pp = ldd(Ar, p * n + pc);
+          const dd a_pq = qcr ? ldd(Ar, p * n + qc) : dd_make(0.f);
           const dd m_p0 = qcr ? rot_combine(cR, a_pp, sR, a_pq, true) : a_pp;
           const dd m_p1 = qcr ? rot_combine(sR, a_pp, cR, a_pq, false) : dd_make(0.f);
           if (q < n) {
-            const dd a_qp = ldd(Ar, (long)q * n + pc);
-            const dd a_qq = qcr ? ldd(Ar, (long)q * n + qc) : dd_make(0.f);
+            const dd a_qp = ldd(Ar, q * n + pc);
+            const dd a_qq = qcr ? ldd(Ar, q * n + qc) : dd_make(0.f);
             const dd m_q0 = qcr ? rot_combine(cR, a_qp, sR, a_qq, true) : a_qp;
             const dd m_q1 = qcr ? rot_combine(sR, a_qp, cR, a_qq, false) : dd_make(0.f);
             // A' = J_P^T M
-            sdd(Bw, (long)p * n + pc, rot_combine(cP, m_p0, sP, m_q0, true));
-            sdd(Bw, (long)q * n + pc, rot_combine(sP, m_p0, cP, m_q0, false));
+            sdd(Bw, p * n + pc, rot_combine(cP, m_p0, sP, m_q0, true));
+            sdd(Bw, q * n + pc, rot_combine(sP, m_p0, cP, m_q0, false));
             if (qcr) {
-              sdd(Bw, (long)p * n + qc, rot_combine(cP, m_p1, sP, m_q1, true));
-              sdd(Bw, (long)q * n + qc, rot_combine(sP, m_p1, cP, m_q1, false));
+              sdd(Bw, p * n + qc, rot_combine(cP, m_p1, sP, m_q1, true));
+              sdd(Bw, q * n + qc, rot_combine(sP, m_p1, cP, m_q1, false));
             }
           } else {
-            sdd(Bw, (long)p * n + pc, m_p0);
-            if (qcr) sdd(Bw, (long)p * n + qc, m_p1);
+            sdd(Bw, p * n + pc, m_p0);
+            if (qcr) sdd(Bw, p * n + qc, m_p1);
           }
         } else if (qcr) {
           const int i = it - half;
-          const dd v0 = ldd(Vw, (long)i * n + pc), v1 = ldd(Vw, (long)i * n + qc);
-          sdd(Vw, (long)i * n + pc, rot_combine(cR, v0, sR, v1, true));
-          sdd(Vw, (long)i * n + qc, rot_combine(sR, v0, cR, v1, false));
+          const dd v0 = ldd(Vw, i * n + pc), v1 = ldd(Vw, i * n + qc);
+          sdd(Vw, i * n + pc, rot_combine(cR, v0, sR, v1, true));
+          sdd(Vw, i * n + qc, rot_combine(sR, v0, cR, v1, false));
         }
       }
       if (!grid_barrier(P)) return;
@@ -277,10 +291,6 @@ __global__ void __launch_bounds__(JNT, 3) jacobi_coop_kernel(JacobiArgs P) {
   }
 }
 
-__global__ void identity_kernel(int n, double* V) {
-  long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (idx < (long)n * n) V[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
-}
 
 // ranks by (value descending | ascending, index ascending)
 __global__ void eig_rank_kernel(int n, const double* __restrict__ A, bool descending, int* rank) {
@@ -358,7 +368,7 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   P.max_sweeps = max_sweeps;
   DSRG_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
   DSRG_CUDA(cudaMemsetAsync(status_dev, 0, 4 * sizeof(int), st));
-  const size_t smem = sizeof(float4) * (size_t)(m / 2);
+  const size_t smem = (sizeof(float4) + sizeof(int2)) * (size_t)(m / 2);
   constexpr int SMEM_CEILING = 200 * 1024;
   if (smem > (size_t)SMEM_CEILING) return DSRG_FNO_ERR_UNSUPPORTED;
   // one fixed ceiling for every launch: concurrent callers (batch workers)
@@ -370,9 +380,10 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   DSRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_coop_kernel, JNT, smem));
   if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
-  // (half + n) * half work units per round; small matrices use few blocks
+  // (half + n) items of half column pairs per round; small matrices use few blocks
   const long units = (long)(m / 2 + n) * (m / 2);
-  int nblk = (int)std::min<long>(std::min(sms * std::min(occ, 3), JMAX_BLOCKS), (units + 8 * JNT - 1) / (8 * JNT));
+  if ((long)n * n >= (1L << 31)) return DSRG_FNO_ERR_UNSUPPORTED;  // 32-bit element offsets
+  int nblk = (int)std::min<long>(std::min(sms * std::min(occ, JACOBI_BLOCKS_PER_SM), JMAX_BLOCKS), (units + 8 * JNT - 1) / (8 * JNT));
   nblk = std::max(nblk, 1);
   void* args[] = {&P};
   DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(nblk), dim3(JNT), args, smem, st));
