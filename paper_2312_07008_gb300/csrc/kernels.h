@@ -40,8 +40,14 @@ enum DressKind {
 };
 
 // outputs per work item; blocks per work item (they stride over upper tiles)
-constexpr int DRESS_OC = 32;
-constexpr int DRESS_TILE_BLOCKS = 24;
+#ifndef DRESS_OUTPUTS
+#define DRESS_OUTPUTS 8
+#endif
+#ifndef DRESS_BLOCKS
+#define DRESS_BLOCKS 48
+#endif
+constexpr int DRESS_OC = DRESS_OUTPUTS;          // outputs of one dressing work item
+constexpr int DRESS_TILE_BLOCKS = DRESS_BLOCKS;  // blocks sharing the tiles of one work item
 
 struct DressAux {
   const double* g1_evec;   // [na][na] (column k)
