@@ -14,7 +14,8 @@ extern "C" {
 #endif
 
 /* C[M][N] = A[M][K] B[N][K]^T with the exact bf16 digit-plane GEMM on the
- * tensor cores (nslices planes, 3..5).  All arrays are host float64,
+ * tensor cores (nslices planes, 3..6; 6 is the configuration the library
+ * uses for the rotation of B to the frozen natural orbitals).  All arrays are host float64,
  * row-major.  This is the contraction kernel of the fast form by itself. */
 int dsrg_fno_debug_sliced_gemm(int32_t nslices, int32_t M, int32_t N, int32_t K, const double* A,
                                const double* B, double* C);

@@ -550,9 +550,13 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
   size_t pass_mo = e2_mo_in ? 0 : energy_pass_bytes(g, ks, budget);
   size_t pass_f = nk > 0 ? energy_pass_bytes(gf, ks, budget) : 0;
   const int kpv = pad64(nv);
+  // B' = B U enters E_vv(FNO) element by element and Delta E is a difference
+  // of two large energies: the rotation takes 6 digit planes (47 fraction
+  // bits) in the fast form, the passes themselves keep ks.
+  const int kx = ks ? 6 : 0;
   size_t xform = 0;
-  if (ks && nk > 0)
-    xform = ws_bytes((size_t)ks * rows * kpv, 2) + ws_bytes(rows, sizeof(int)) + ws_bytes((size_t)ks * nk * kpv, 2) +
+  if (kx && nk > 0)
+    xform = ws_bytes((size_t)kx * rows * kpv, 2) + ws_bytes(rows, sizeof(int)) + ws_bytes((size_t)kx * nk * kpv, 2) +
             ws_bytes(nk, sizeof(int)) + ws_bytes(8, sizeof(int));
   DSRG_TRY(ws_reserve(ws, fixed + std::max(std::max(pass_mo, pass_f), xform)));
   int* flag = ws_take<int>(ws, 8);
@@ -588,17 +592,17 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
     DSRG_TRY(copy_active(rows, g.na, g.np, gf.np, prob->B_hp, Bf, st));
     if (ks) {
       ws.off = base;
-      __nv_bfloat16* pa = ws_take<__nv_bfloat16>(ws, (size_t)ks * rows * kpv);
+      __nv_bfloat16* pa = ws_take<__nv_bfloat16>(ws, (size_t)kx * rows * kpv);
       int* ea = ws_take<int>(ws, rows);
-      __nv_bfloat16* pb = ws_take<__nv_bfloat16>(ws, (size_t)ks * nk * kpv);
+      __nv_bfloat16* pb = ws_take<__nv_bfloat16>(ws, (size_t)kx * nk * kpv);
       int* eb = ws_take<int>(ws, nk);
       int* err = ws_take<int>(ws, 8);
       if (!err) return DSRG_FNO_ERR_NOMEM;
       DSRG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
       // rows (Q, h) over the virtual index e, and U^T rows l over e
-      DSRG_TRY(slice_rows(ks, prob->B_hp + g.na, rows, nv, g.np, 1, kpv, pa, ea, st));
-      DSRG_TRY(slice_rows(ks, U, nk, nv, 1, nk, kpv, pb, eb, st));
-      DSRG_TRY(sliced_plain_gemm(ks, (int)rows, nk, pa, ea, pb, eb, kpv, Bf + g.na, gf.np, err, st));
+      DSRG_TRY(slice_rows(kx, prob->B_hp + g.na, rows, nv, g.np, 1, kpv, pa, ea, st));
+      DSRG_TRY(slice_rows(kx, U, nk, nv, 1, nk, kpv, pb, eb, st));
+      DSRG_TRY(sliced_plain_gemm(kx, (int)rows, nk, pa, ea, pb, eb, kpv, Bf + g.na, gf.np, err, st));
       DSRG_TRY(read_error_flag(err, st));
     } else {
       DSRG_TRY(gemm_f64((int)rows, nk, nv, 1.0, prob->B_hp + g.na, g.np, true, U, nk, false, 0.0, Bf + g.na, gf.np,

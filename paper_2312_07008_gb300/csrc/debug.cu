@@ -19,7 +19,7 @@ struct DevBuf {
 
 extern "C" int dsrg_fno_debug_sliced_gemm(int32_t ks, int32_t M, int32_t N, int32_t K, const double* A,
                                           const double* B, double* C) {
-  if (ks < 3 || ks > 5 || M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return DSRG_FNO_ERR_ARG;
+  if (ks < 3 || ks > 6 || M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return DSRG_FNO_ERR_ARG;
   const int kp = pad64(K);
   DevBuf dA, dB, dC, pa, pb, ea, eb, err;
   DSRG_CUDA(cudaMalloc(&dA.p, sizeof(double) * M * K));
@@ -47,7 +47,7 @@ extern "C" int dsrg_fno_debug_sliced_gemm(int32_t ks, int32_t M, int32_t N, int3
 
 extern "C" int dsrg_fno_debug_slice_rows(int32_t ks, int32_t R, int32_t K, const double* rows, float* planes,
                                          int32_t* exps) {
-  if (ks < 3 || ks > 5 || R <= 0 || K <= 0 || !rows || !planes || !exps) return DSRG_FNO_ERR_ARG;
+  if (ks < 3 || ks > 6 || R <= 0 || K <= 0 || !rows || !planes || !exps) return DSRG_FNO_ERR_ARG;
   const int kp = pad64(K);
   DevBuf d, p, e;
   DSRG_CUDA(cudaMalloc(&d.p, sizeof(double) * R * K));

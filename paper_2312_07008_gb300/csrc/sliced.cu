@@ -29,6 +29,8 @@
 // bounded; on expiry the kernel records the failure and leaves.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -68,7 +70,7 @@ __device__ __forceinline__ void digits_of(double v, int e_row, int* d) {
   long long X = 0;
   if (E != 0) {
     long long m = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-    int sh = 1075 - E - F + e_row;  // >= 14 for KS <= 5 because |v| < 2^e_row
+    int sh = 1075 - E - F + e_row;  // >= 53 - F >= 6 for KS <= 6 because |v| < 2^e_row
     if (sh < 63) X = (m + (1LL << (sh - 1))) >> sh;
     if (b < 0) X = -X;
   }
@@ -789,11 +791,14 @@ int dispatch_gemm(int KS, const void* pa, long rows_a, const void* pb, long rows
     case 3: return launch_gemm<3, 64, 3, GEMM_CLUSTER>(pa, rows_a, pb, rows_b, Kpad, P, st);
     case 4: return launch_gemm<4, 64, 2, GEMM_CLUSTER>(pa, rows_a, pb, rows_b, Kpad, P, st);
     case 5: return launch_gemm<5, 48, 2, GEMM_CLUSTER>(pa, rows_a, pb, rows_b, Kpad, P, st);
+    // 6 planes (21 products): TMEM allows N = 32, shared memory one stage
+    case 6: return P.mode == MODE_PLAIN ? launch_gemm<6, 32, 1, 1>(pa, rows_a, pb, rows_b, Kpad, P, st)
+                                        : DSRG_FNO_ERR_ARG;
     default: return DSRG_FNO_ERR_ARG;
   }
 }
 
-int tile_n_for(int KS) { return KS == 5 ? 48 : 64; }
+int tile_n_for(int KS) { return KS == 6 ? 32 : (KS == 5 ? 48 : 64); }
 
 }  // namespace
 
@@ -807,6 +812,13 @@ static int slice_rows_t(int KS, const T* src, long R, int K, long rs, long ks, i
     case 3: slice_rows_kernel<3, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps, rowmax); break;
     case 4: slice_rows_kernel<4, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps, rowmax); break;
     case 5: slice_rows_kernel<5, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps, rowmax); break;
+    case 6:  // float64 rows only (47 fraction bits; the double-float path keeps <= 5 planes)
+      if constexpr (std::is_same<T, double>::value) {
+        slice_rows_kernel<6, T><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps, rowmax);
+        break;
+      } else {
+        return DSRG_FNO_ERR_ARG;
+      }
     default: return DSRG_FNO_ERR_ARG;
   }
   DSRG_LAUNCH_CHECK();
