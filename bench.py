@@ -336,7 +336,8 @@ def main():
                                     **{f"de_{c}": res[c][1] - r64[c][1] for c in cuts},
                                     **{f"nkept_{c}": [res[c][0], r64[c][0]] for c in cuts}}}
 
-    roofline = roofline_of(pair_ms, pair_n, pair_fl, (syrk_ms, syrk_n, syrk_fl), (plain_ms, plain_n, plain_fl), ms)
+    roofline = roofline_of(pair_ms, pair_n, pair_fl, (syrk_ms, syrk_n, syrk_fl), (plain_ms, plain_n, plain_fl), ms,
+                           args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -363,14 +364,48 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline_of(pair_ms, pair_n, pair_fl, syrk, plain, step_ms):
+# DRAM bytes per executed flop of the pair contraction, from one ncu capture
+# of a full-size pair launch of this workload (the summary in profiles/ names
+# the command); valid only for the kernel sources it was taken with.
+TRAFFIC = {
+    "sa_cas10_ncore60_nvir1200_naux3600": {
+        "bytes_per_exec_flop": 214.409e9 / 1.178e14,
+        "sha256": {"paper_2312_07008_gb300/csrc/sliced.cu":
+                   "5c650e818ef0ea227c67a35a9bcc65831371be56f4ddd26ff2c02170b1b64479",
+                   "paper_2312_07008_gb300/csrc/tc_ptx.cuh":
+                   "970edeabe7cd01f635dc03045d58bcc21657742d5a046bc2110ab8b012c97aed"},
+    },
+}
+
+
+def traffic_per_launch(workload, exec_flops_per_launch):
+    """DRAM bytes of an average pair launch, or None when no capture matches
+    the current kernel sources."""
+    import hashlib
+    t = TRAFFIC.get(workload)
+    if t is None:
+        return None
+    for rel, digest in t["sha256"].items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return t["bytes_per_exec_flop"] * exec_flops_per_launch
+
+
+def roofline_of(pair_ms, pair_n, pair_fl, syrk, plain, step_ms, workload=None):
     peaks, peak_kind = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     achieved = (pair_fl / (pair_ms / 1e3) / 1e12) if pair_ms > 0 else None
     tf = lambda q: (q[2] / (q[0] / 1e3) / 1e12) if q[0] > 0 else None  # noqa: E731
     return {"bound": "tensor", "kernel": "sliced_gemm_kernel (pair contraction, tcgen05 bf16 digit planes)",
             "achieved": achieved, "peak": peak, "peak_kind": f"bf16 dense sustained, {peak_kind}",
-            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic_per_launch(workload, pair_fl / max(pair_n, 1)) if pair_n else None,
+            "traffic_note": "DRAM bytes per average pair launch: bytes per executed flop from one ncu capture of "
+                            "a full-size pair launch, times this run's executed flops per launch",
             "launches": pair_n, "avg_launch_ms": pair_ms / max(pair_n, 1),
             "executed_flops_per_launch": pair_fl / max(pair_n, 1),
             "share_of_step": pair_ms / step_ms if step_ms > 0 else None,
