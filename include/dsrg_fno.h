@@ -97,7 +97,11 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
  *   dvv       device [nvir][nvir], symmetric, read only.
  *   mode      0: p_o (Eq. 10, threshold in percent of the summed ONs);
  *             1: p_v (Eq. 9, threshold in percent of nvir, rounded up);
- *             2: n_kappa (keep ONs >= threshold).
+ *             2: n_kappa (keep ONs >= threshold);
+ *             3: a fixed N' = threshold (rounded, clamped to [0, nvir]): the
+ *                same number of virtuals at every geometry of a potential
+ *                energy surface, which Sec. 4 suggests against the jumps a
+ *                cumulative cut makes (pass degen_ratio 0 to keep N' exact).
  *   degen_ratio  near-degeneracy widening: while the next ON differs from the
  *             last kept one by less than degen_ratio times the larger, keep it
  *             (0.01 in the paper); 0 disables.

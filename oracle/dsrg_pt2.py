@@ -379,7 +379,7 @@ def natural_orbitals(d):
     return w, v * sgn[None, :]
 
 
-MODE_PO, MODE_PV, MODE_NKAPPA = 0, 1, 2
+MODE_PO, MODE_PV, MODE_NKAPPA, MODE_FIXED = 0, 1, 2, 3
 
 
 def truncate(ons, mode: int, threshold: float, degen_ratio: float = 0.01):
@@ -388,6 +388,8 @@ def truncate(ons, mode: int, threshold: float, degen_ratio: float = 0.01):
     mode 0 (p_o, Eq. 10): smallest N' with sum_{p<=N'} n_p >= p_o/100 * sum_all n_p
     mode 1 (p_v, Eq. 9):  N' = ceil(p_v/100 * N_V)
     mode 2 (n_kappa):     number of ONs >= n_kappa
+    mode 3 (fixed):       N' = threshold, rounded and clamped to [0, N_V] (the
+                          same N' along a potential energy surface, Sec. 4)
     Then the near-degeneracy widening: while N' < N_V and the next ON differs
     from the last kept one by less than degen_ratio times the larger of the
     two, keep it as well."""
@@ -402,6 +404,8 @@ def truncate(ons, mode: int, threshold: float, degen_ratio: float = 0.01):
         k = int(np.ceil(threshold / 100.0 * nv - 1e-12))
     elif mode == MODE_NKAPPA:
         k = int(np.count_nonzero(n >= threshold))
+    elif mode == MODE_FIXED:
+        k = int(np.rint(min(max(threshold, 0.0), float(nv))))
     else:
         raise ValueError("mode")
     k = max(0, min(nv, k))

@@ -38,7 +38,7 @@ EXPORTED = (
 
 FP64 = 0
 SLICED_BF16 = 1
-MODE_PO, MODE_PV, MODE_NKAPPA = 0, 1, 2
+MODE_PO, MODE_PV, MODE_NKAPPA, MODE_FIXED = 0, 1, 2, 3
 
 
 class DsrgFnoError(RuntimeError):

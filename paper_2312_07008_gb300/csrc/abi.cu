@@ -505,7 +505,7 @@ int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, dou
 int impl_truncate(Workspace& ws, int32_t nvir, const double* dvv, int32_t mode, double threshold,
                          double degen_ratio, double* on_out, double* no_out, int32_t* nkept_out, cudaStream_t st) {
   if (nvir <= 0 || !dvv || !on_out || !no_out || !nkept_out) return DSRG_FNO_ERR_ARG;
-  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  if (mode < 0 || mode > 3 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
   if (!is_device_ptr(dvv) || !is_device_ptr(on_out) || !is_device_ptr(no_out)) return DSRG_FNO_ERR_ARG;
   const size_t n2 = (size_t)nvir * nvir;
   DSRG_TRY(ws_reserve(ws, 2 * doubles(n2) + doubles(eig_work_doubles(nvir)) + ws_bytes(nvir + 8, sizeof(int))));
@@ -681,7 +681,7 @@ int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double thre
 int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold, double degen_ratio,
                  int32_t* nkept_out, void* stream) {
   if (nvir <= 0 || !ons || !nkept_out || !is_device_ptr(ons)) return DSRG_FNO_ERR_ARG;
-  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  if (mode < 0 || mode > 3 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();

@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(256) pair_epilogue_dd_kernel(Geometry g, const
   __syncthreads();
   const dd s = dd_from_double(g.s);
   const int rows = min(EPI_ROWS, np - a0);
-  for (int idx = threadIdx.x; idx < rows * np; idx += blockDim.x) {
-    const int a = a0 + idx / np, b = idx % np;
+  for (int ra = 0; ra < rows; ++ra)
+  for (int b = threadIdx.x; b < np; b += blockDim.x) {
+    const int a = a0 + ra;
     const bool av = a >= na, bv = b >= na;
     if (!av && !bv) continue;
     if (ts == nullptr && !(av && bv)) continue;

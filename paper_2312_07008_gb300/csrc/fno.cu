@@ -29,6 +29,8 @@ __global__ void truncate_kernel(int nv, const double* __restrict__ ons, int mode
     }
   } else if (mode == 1) {
     k = (int)ceil(thr / 100.0 * nv - 1e-12);
+  } else if (mode == 3) {
+    k = (int)rint(fmin(fmax(thr, 0.0), (double)nv));
   } else {
     k = 0;
     for (int p = 0; p < nv; ++p) k += (ons[p] >= thr) ? 1 : 0;

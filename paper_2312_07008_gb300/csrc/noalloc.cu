@@ -59,7 +59,7 @@ extern "C" int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_
     return DSRG_FNO_ERR_ARG;
   }
   if (nvir <= 0 || !dvv || !on_out || !no_out || !nkept_out) return DSRG_FNO_ERR_ARG;
-  if (mode < 0 || mode > 2 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  if (mode < 0 || mode > 3 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* base = nullptr;
   DSRG_TRY(noalloc_scratch(&base));

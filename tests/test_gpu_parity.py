@@ -107,7 +107,7 @@ def test_truncation_modes_match_oracle():
     d = torch.from_numpy(ref_d).cuda()
     on = torch.empty(60, dtype=torch.float64, device="cuda")
     no = torch.empty((60, 60), dtype=torch.float64, device="cuda")
-    for mode, thr in ((0, 95.0), (0, 100.0), (1, 25.0), (1, 100.0), (2, 1e-3), (2, 1e3)):
+    for mode, thr in ((0, 95.0), (0, 100.0), (1, 25.0), (1, 100.0), (2, 1e-3), (2, 1e3), (3, 17.0), (3, 60.0)):
         for ratio in (0.01, 0.0, 0.5):
             k = pkg.dsrg_fno_truncate(60, d, mode, thr, ratio, on, no)
             assert k == O.truncate(n_ref, mode, thr, ratio), (mode, thr, ratio)

@@ -309,6 +309,11 @@ def test_natural_orbitals_against_lapack():
     ([1.0, 0.995, 0.9852, 0.5], 0, 30.0, 3),    # widening chain 1 -> 2 -> 3
     ([1.0, 0.99, 0.5, 0.49], 0, 30.0, 1),       # 0.01 difference is not < 0.01
     ([1.0, 0.5, 0.496, -1e-6], 0, 85.0, 3),     # negative ON in the denominator
+    ([4.0, 3.0, 2.0, 1.0], 3, 2.0, 2),          # fixed N'
+    ([4.0, 3.0, 2.0, 1.0], 3, 2.6, 3),          # rounded
+    ([4.0, 3.0, 2.0, 1.0], 3, 9.0, 4),          # clamped to N_V
+    ([4.0, 3.0, 2.0, 1.0], 3, -1.0, 0),
+    ([1.0, 0.995, 0.9852, 0.5], 3, 1.0, 3),     # widening still applies
 ])
 def test_truncation_rules(ons, mode, thr, expect):
     assert O.truncate(np.array(ons), mode, thr, 0.01) == expect
