@@ -216,15 +216,20 @@ static long pair_cap_for_budget(int nv, int np, int ks, size_t budget) {
   return std::max<long>(cap, 1);
 }
 
-size_t device_budget() {
+// 45 % of the free device memory, counting `held` bytes that the caller's
+// own workspaces already occupy as free (capped at 48 GB): the plan of a pass
+// then does not depend on what earlier calls allocated.
+size_t device_budget(size_t held) {
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
     return (size_t)4 << 30;
   }
-  size_t b = (size_t)(0.45 * (double)fr);
+  size_t b = (size_t)(0.45 * (double)(fr + held));
   return std::min(b, (size_t)48 << 30);
 }
+
+static size_t plan_budget(const Workspace& ws) { return device_budget(ws.cap); }
 
 static int run_pass(const Geometry& g, const double* B, const double* eps, const double* gamma1,
                     const double* lambda2, const Plan& P, PassBuffers& W, bool want_d, double* D,
@@ -662,13 +667,13 @@ void dsrg_fno_release(void) {
 int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stream) {
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
-  return impl_pt2_energy(ws, device_budget() + ws.cap / 2, prob, e2_out, (cudaStream_t)stream);
+  return impl_pt2_energy(ws, plan_budget(ws), prob, e2_out, (cudaStream_t)stream);
 }
 
 int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out, void* stream) {
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
-  return impl_vv_opdm(ws, device_budget() + ws.cap / 2, prob, dvv_out, e2_out, (cudaStream_t)stream);
+  return impl_vv_opdm(ws, plan_budget(ws), prob, dvv_out, e2_out, (cudaStream_t)stream);
 }
 
 int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,
@@ -700,7 +705,7 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
                                   double* eps_fno_out, void* stream) {
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
-  return impl_correction(ws, device_budget() + ws.cap / 2, prob, nkept, no, e2_mo_in, de_out, e2_fno_out, eps_fno_out,
+  return impl_correction(ws, plan_budget(ws), prob, nkept, no, e2_mo_in, de_out, e2_fno_out, eps_fno_out,
                          (cudaStream_t)stream);
 }
 

@@ -140,7 +140,7 @@ extern "C" int dsrg_fno_batch_run(dsrg_fno_batch_item* items, int32_t n, int32_t
   // each worker plans its passes within an equal share of the free memory
   size_t have = 0;
   for (int k = 0; k < workers; ++k) have += pool.w[k].ws.cap;
-  const size_t share = (device_budget() + have / 2) / (size_t)workers;
+  const size_t share = device_budget(have) / (size_t)workers;
 
   const auto t0 = std::chrono::steady_clock::now();
   std::atomic<int> next{0};

@@ -134,7 +134,7 @@ int check_finite(const double* x, long n, int* flag, cudaStream_t st);
 // Single-instance pipeline stages on an explicit workspace (abi.cu); the C
 // entry points call them on the per-device workspace, the batch runner on
 // its workers' workspaces.  `budget`: device bytes a pass may plan for.
-size_t device_budget();
+size_t device_budget(size_t held);
 void release_batch_pools();  // batch.cu
 int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* e2_out, cudaStream_t st);
 int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
