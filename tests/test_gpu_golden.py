@@ -1,6 +1,6 @@
 """Full-size workloads against stored oracle values (tests/golden/*.json).
 
-The oracle cannot rerun the full-size workloads inside a test (C2 takes
+The oracle cannot rerun the full-size workloads inside a test (nvir 1200 takes
 about an hour on eight cores), so tests/golden/make_golden.py stored its
 results once; here the CUDA path, in both arithmetic forms and in the launch
 configuration the benchmark uses, is compared with them: E_vv, every ON,
