@@ -54,6 +54,21 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, dist, device):
+    """Largest value of `x` over the ranks (the slowest replica sets the time)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput of weakly scaled replicas: all ranks' units over
+    the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def algorithmic_flops(p):
     """F_V + F_D per solve: naux nvir^2 nh (nh+1) + nh^2 nvir^3."""
     nh = p.ncore + p.nact
@@ -278,12 +293,8 @@ def main():
     pair_ms, pair_n, pair_fl = pkg.dsrg_fno_profile_query("sliced_gemm_pair")
     syrk_ms, syrk_n, syrk_fl = pkg.dsrg_fno_profile_query("sliced_gemm_syrk")
     plain_ms, plain_n, plain_fl = pkg.dsrg_fno_profile_query("sliced_gemm_plain")
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    solves = args.steps * world
-    value = solves / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = replica_rate(args.steps, world, ms_max)
     flops = algorithmic_flops(p)
 
     # ---- end to end through the C ABI, host buffers in pinned memory
@@ -312,10 +323,7 @@ def main():
         e2e_step()
     e1.record(stream)
     barrier()
-    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = solves / (float(te.item()) / 1e3)
+    e2e_value = replica_rate(args.steps, world, max_over_ranks(e0.elapsed_time(e1), dist, dev))
     clocks = clk.stop()  # sampled over the device-timed and the end-to-end steps
 
     # ---- the plain float64 GPU form of the same solve
@@ -482,11 +490,8 @@ def batch_arm(args):
     for nm in PHASES:
         t_ms, n_l, _ = pkg.dsrg_fno_profile_query(nm)
         phases[nm] = {"stream_ms_per_step": t_ms / args.steps, "launches_or_calls": n_l}
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = args.steps * world * n / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = replica_rate(args.steps * n, world, ms_max)
     flops = sum(algorithmic_flops(p) for p in probs)
 
     # ---- end to end: every instance's inputs from pinned host memory each step
@@ -521,10 +526,7 @@ def batch_arm(args):
         e2e_step()
     e1.record(stream)
     barrier()
-    te = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = args.steps * world * n / (float(te.item()) / 1e3)
+    e2e_value = replica_rate(args.steps * n, world, max_over_ranks(e0.elapsed_time(e1), dist, dev))
 
     # ---- the float64 GPU form on every 4th instance (a 16-instance sample)
     fp64 = None
