@@ -6,6 +6,7 @@ results once; here the CUDA path, in both arithmetic forms and in the launch
 configuration the benchmark uses, is compared with them: E_vv, every ON,
 diag and row 0 of D_vv, N' and the correction of every cut.
 """
+import functools
 import glob
 import json
 import os
@@ -24,6 +25,11 @@ import paper_2312_07008_gb300 as pkg  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 FILES = sorted(glob.glob(os.path.join(HERE, "golden", "*.json")))
+
+
+@functools.lru_cache(maxsize=None)
+def problem(name):
+    return workload(name)  # generated once for both arithmetic forms
 
 
 def run(p, cuts, precision):
@@ -49,7 +55,7 @@ def run(p, cuts, precision):
 @pytest.mark.parametrize("path", FILES, ids=[os.path.basename(f)[:-5] for f in FILES])
 def test_workload_matches_stored_oracle(path, precision):
     ref = json.load(open(path))
-    p = workload(ref["workload"])
+    p = problem(ref["workload"])
     cuts = [float(c) for c in ref["cuts"]]
     got = run(p, cuts, precision)
     e_tol = 1e-7 if precision == pkg.SLICED_BF16 else 1e-8
