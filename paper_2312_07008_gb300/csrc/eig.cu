@@ -96,13 +96,19 @@ __device__ __forceinline__ void sdd(float2* p, int i, dd v) { __stcg(p + i, make
 // c a +- s b with double-float operands.  The sum keeps an absolute error
 // of a few units of 2^-48 max(|c a|, |s b|), which is what the backward
 // stability of the rotations needs (no relative accuracy under cancellation).
+// The two products' high parts are exact (FMA TwoProduct) and summed with
+// TwoSum; their low parts and the cross terms go into one float32 word.
 __device__ __forceinline__ dd rot_combine(dd ca, dd a, dd sb, dd b, bool minus) {
-  const dd x = dd_mul(ca, a);
-  dd y = dd_mul(sb, b);
-  if (minus) y = dd_neg(y);
-  dd t = two_sum(x.hi, y.hi);
-  t.lo = __fadd_rn(t.lo, __fadd_rn(x.lo, y.lo));
-  return quick_two_sum(t.hi, t.lo);
+  const float sh = minus ? -sb.hi : sb.hi, sl = minus ? -sb.lo : sb.lo;
+  const float ph = __fmul_rn(ca.hi, a.hi), pl = __fmaf_rn(ca.hi, a.hi, -ph);
+  const float qh = __fmul_rn(sh, b.hi), ql = __fmaf_rn(sh, b.hi, -qh);
+  dd t = two_sum(ph, qh);
+  float lo = __fadd_rn(t.lo, __fadd_rn(pl, ql));
+  lo = __fmaf_rn(ca.hi, a.lo, lo);
+  lo = __fmaf_rn(ca.lo, a.hi, lo);
+  lo = __fmaf_rn(sh, b.lo, lo);
+  lo = __fmaf_rn(sl, b.hi, lo);
+  return quick_two_sum(t.hi, lo);
 }
 
 // 1 / sqrt(x) for x in [1, 2] in double-float: float estimate, two Newton steps
