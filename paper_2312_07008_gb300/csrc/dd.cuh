@@ -43,6 +43,16 @@ __device__ __forceinline__ dd dd_add(dd a, dd b) {
 }
 
 __device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
+
+// a + b with an absolute error of a few units of 2^-48 max(|a|, |b|) (no
+// relative accuracy when the high parts cancel); for sums whose terms keep
+// their sign or whose cancellation the caller does not need resolved.
+__device__ __forceinline__ dd dd_add_fast(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_sub_fast(dd a, dd b) { return dd_add_fast(a, dd_neg(b)); }
 __device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
 
 __device__ __forceinline__ dd dd_add_f(dd a, float b) {

@@ -79,13 +79,13 @@ __device__ __forceinline__ void regularize(dd delta, dd s, const RegTables& R, d
   const dd u2 = dd_mul(u, u);
   const dd c3 = dd_mul(dd_mul(u2, u), R.sixth);
   const float tail = uh * uh * uh * uh * (1.0f / 24.0f - uh * (1.0f / 120.0f - uh * (1.0f / 720.0f)));
-  const dd omp = dd_add_f(dd_add(dd_sub(u, dd_mul_f(u2, 0.5f)), c3), -tail);
-  const dd p = dd_sub(dd_make(1.0f), omp);
+  const dd omp = dd_add_f(dd_add_fast(dd_sub_fast(u, dd_mul_f(u2, 0.5f)), c3), -tail);
+  const dd p = dd_sub_fast(dd_make(1.0f), omp);
   const int q = n >> 6, j = n & 63;
   *y = dd_ldexp(dd_mul(R.T[j], p), -q);
   dd omy;
-  if (q == 0) omy = dd_add(R.C[j], dd_sub(omp, dd_mul(R.C[j], omp)));
-  else omy = dd_sub(dd_make(1.0f), *y);
+  if (q == 0) omy = dd_add_fast(R.C[j], dd_sub_fast(omp, dd_mul(R.C[j], omp)));
+  else omy = dd_sub_fast(dd_make(1.0f), *y);
   *r1 = dd_div(omy, delta);
 }
 
@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
       // the two signed combinations are formed once per slot
       const float du = (float)dg[u];
       const dd att = {du * tT[tx][ty].x, du * tT[tx][ty].y}, btt = {du * tK[tx][ty].x, du * tK[tx][ty].y};
-      const dd tp = dd_add(a, att), tm = dd_sub(a, att);
-      const dd kp = dd_add(b, btt), km = dd_sub(b, btt);
+      const dd tp = dd_add_fast(a, att), tm = dd_sub_fast(a, att);
+      const dd kp = dd_add_fast(b, btt), km = dd_sub_fast(b, btt);
 #pragma unroll
       for (int o = 0; o < OCT; ++o) {
         if (o < oc) {
