@@ -303,12 +303,34 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
   return DSRG_FNO_OK;
 }
 
-static int nsplit_for(int nv, int ndesc) {
-  const int nt = ceil_div(nv, 64);
-  const int tiles = nt * (nt + 1) / 2;
-  int ns = ceil_div(2L * 152, tiles);
-  ns = std::min(ns, std::max(ndesc, 1));
-  return std::max(ns, 1);
+// Split of the dressed rank-K update over the dressed matrices: enough
+// upper-triangle tile jobs for two waves of the SMs, and a count that fills
+// its last wave (jobs = tiles x splits, the persistent grid has one CTA per SM).
+static int nsplit_for(int nv, int ndesc, int ks) {
+  int tiles;
+  if (ks) {  // 128 x BN tiles of the digit-plane kernel with some f >= e
+    const int bm = 128, bn = ks == 5 ? 48 : 64;
+    const int ntm = ceil_div(nv, bm), ntn = ceil_div(nv, bn);
+    tiles = 0;
+    for (int m = 0; m < ntm; ++m) tiles += ntn - (m * bm) / bn;
+  } else {   // 64 x 64 upper tiles of the float64 kernel
+    const int nt = ceil_div(nv, 64);
+    tiles = nt * (nt + 1) / 2;
+  }
+  const int sms = 152;
+  const int cap = std::max(1, std::min(16, ndesc));
+  int best = std::min(cap, std::max(1, ceil_div(2L * sms, tiles)));
+  double best_eff = 0.0;
+  for (int ns = best; ns <= cap; ++ns) {
+    const long jobs = (long)tiles * ns;
+    const double eff = (double)jobs / ((double)ceil_div(jobs, (long)sms) * sms);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = ns;
+    }
+    if (eff >= 0.97) break;
+  }
+  return best;
 }
 
 // Carves the pass buffers out of the workspace (sizes must match pass_bytes).
@@ -460,7 +482,7 @@ int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, dou
   const int ks = slices_of(prob);
   Plan P;
   build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, budget), P);
-  const int nsplit = nsplit_for(g.nv, P.max_out);
+  const int nsplit = nsplit_for(g.nv, P.max_out, ks);
   const size_t small = small_terms_work_doubles(g.nc, g.na, g.nv);
   const int kmax = small_terms_kmax(g.nc, g.na);
   const bool small_fast = ks > 0 && kmax >= SLICED_MIN_K;
