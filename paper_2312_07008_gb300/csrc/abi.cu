@@ -217,7 +217,7 @@ static long pair_cap_for_budget(int nv, int np, int ks, size_t budget) {
 }
 
 // 45 % of the free device memory, counting `held` bytes that the caller's
-// own workspaces already occupy as free (capped at 48 GB): the plan of a pass
+// own workspaces already occupy as free (capped at 96 GB): the plan of a pass
 // then does not depend on what earlier calls allocated.
 size_t device_budget(size_t held) {
   size_t fr = 0, tot = 0;
@@ -226,7 +226,7 @@ size_t device_budget(size_t held) {
     return (size_t)4 << 30;
   }
   size_t b = (size_t)(0.45 * (double)(fr + held));
-  return std::min(b, (size_t)48 << 30);
+  return std::min(b, (size_t)96 << 30);
 }
 
 static size_t plan_budget(const Workspace& ws) { return device_budget(ws.cap); }
