@@ -34,6 +34,7 @@ namespace {
 constexpr int JNT = JACOBI_THREADS;      // threads per block
 constexpr int JMAX_BLOCKS = EIG_MAX_BLOCKS;
 constexpr long long BAR_SPIN_LIMIT = 20000000;  // ~2 s of 100 ns naps
+constexpr int SMEM_JACOBI_N = 80;               // largest n solved in shared memory (150 KB)
 
 // index at position pos of round r (position 0 fixed, the others rotate)
 __device__ __forceinline__ int rr_index(int pos, int r, int m) {
@@ -93,6 +94,27 @@ __device__ __forceinline__ dd ldd(const float2* p, int i) {
 }
 __device__ __forceinline__ void sdd(float2* p, int i, dd v) { __stcg(p + i, make_float2(v.hi, v.lo)); }
 
+// A, the ping-pong copy and V live in global memory (L2, bypassing L1 since
+// other blocks write them), or, for a one-block solve of a small matrix, in
+// shared memory (SM = true).
+template <bool SM>
+__device__ __forceinline__ dd ldx(const float2* p, int i) {
+  if (SM) {
+    const float2 v = p[i];
+    return {v.x, v.y};
+  }
+  return ldd(p, i);
+}
+template <bool SM>
+__device__ __forceinline__ void stx(float2* p, int i, dd v) {
+  if (SM) p[i] = make_float2(v.hi, v.lo);
+  else sdd(p, i, v);
+}
+template <bool SM>
+__device__ __forceinline__ float2 ldx2(const float2* p, long i) {
+  return SM ? p[i] : __ldcg(p + i);
+}
+
 // c a +- s b with double-float operands.  The sum keeps an absolute error
 // of a few units of 2^-48 max(|c a|, |s b|), which is what the backward
 // stability of the rotations needs (no relative accuracy under cancellation).
@@ -123,12 +145,13 @@ __device__ __forceinline__ dd dd_rsqrt12(dd x) {
 }
 
 // squared off-diagonal and total Frobenius norms of A (fixed summation order)
+template <bool SM>
 __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double* tot) {
   __shared__ double s_o[JNT], s_t[JNT];
   double o = 0.0, t = 0.0;
   const int n2 = P.n * P.n;
   for (int idx = blockIdx.x * JNT + threadIdx.x; idx < n2; idx += gridDim.x * JNT) {
-    const float2 v = __ldcg(A + idx);
+    const float2 v = ldx2<SM>(A, idx);
     const double a = (double)v.x + (double)v.y;
     t += a * a;
     if (idx / P.n != idx % P.n) o += a * a;
@@ -160,20 +183,25 @@ __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double*
   *tot = st;
 }
 
+template <bool SM>
 __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(JacobiArgs P) {
-  // per pair k of the round: c (hi, lo), s (hi, lo), then the pair (p < q)
+  // per pair k of the round: c (hi, lo), s (hi, lo), then the pair (p < q);
+  // with SM, then A, its ping-pong copy and V (n^2 float2 each)
   extern __shared__ float4 s_cs[];
   int2* s_pq = reinterpret_cast<int2*>(s_cs + P.m / 2);
   const int n = P.n, m = P.m, half = m / 2;
   const long n2 = (long)n * n;
+  float2* const A0 = SM ? reinterpret_cast<float2*>(s_cs + P.m) : P.A0;  // after s_pq (8 B x m/2 <= 16 B x m/2)
+  float2* const A1 = SM ? A0 + n2 : P.A1;
+  float2* const VV = SM ? A1 + n2 : P.V;
   for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
     const dd a = dd_from_double(P.A_in[idx]);
-    sdd(P.A0, idx, a);
-    sdd(P.V, idx, dd_make(idx / n == idx % n ? 1.0f : 0.0f));
+    stx<SM>(A0, (int)idx, a);
+    stx<SM>(VV, (int)idx, dd_make(idx / n == idx % n ? 1.0f : 0.0f));
   }
   if (!grid_barrier(P)) return;
-  float2* A = P.A0;
-  float2* B = P.A1;
+  float2* A = A0;
+  float2* B = A1;
   // rounding floor of a converged double-float sweep, relative and squared
   const double tol = fmax(1e-30, ((double)n * 4e-15) * ((double)n * 4e-15));
   double prev = -1.0;
@@ -181,7 +209,7 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
   for (int sweep = 0; sweep <= P.max_sweeps; ++sweep) {
     sweeps_done = sweep;
     double off, tot;
-    norms(P, A, &off, &tot);
+    norms<SM>(P, A, &off, &tot);
     if (off < 0.0) return;
     if (tot == 0.0 || off <= tol * tot || (off <= 1e-22 * tot && prev >= 0.0 && off > 0.25 * prev)) {
       converged = 1;
@@ -196,9 +224,9 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
         const int p = min(i1, i2), q = max(i1, i2);
         float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
         if (q < n) {
-          const dd apq = dd_mul_f(dd_add(ldd(A, p * n + q), ldd(A, q * n + p)), 0.5f);
+          const dd apq = dd_mul_f(dd_add(ldx<SM>(A, p * n + q), ldx<SM>(A, q * n + p)), 0.5f);
           if (apq.hi != 0.0f) {
-            const dd d = dd_sub(ldd(A, q * n + q), ldd(A, p * n + p));
+            const dd d = dd_sub(ldx<SM>(A, q * n + q), ldx<SM>(A, p * n + p));
             const float th = d.hi / (2.0f * apq.hi);
             const float t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
             dd c = dd_rsqrt12(dd_add_f(two_prod(t, t), 1.0f));
@@ -220,7 +248,7 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
       const int ntasks = (half + n) * nchunks;
       const float2* __restrict__ Ar = A;
       float2* __restrict__ Bw = B;
-      float2* __restrict__ Vw = P.V;
+      float2* __restrict__ Vw = VV;
       const int lane = threadIdx.x & 31;
       const int nwarps = gridDim.x * (JNT / 32);
 #pragma unroll 2
@@ -239,31 +267,31 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
           const float4 rc = s_cs[it];
           const dd cP = {rc.x, rc.y}, sP = {rc.z, rc.w};
           // M = A[{p,q}, {pc,qc}] J_R
-          const dd a_pp = ldd(Ar, p * n + pc);
-          const dd a_pq = qcr ? ldd(Ar, p * n + qc) : dd_make(0.f);
+          const dd a_pp = ldx<SM>(Ar, p * n + pc);
+          const dd a_pq = qcr ? ldx<SM>(Ar, p * n + qc) : dd_make(0.f);
           const dd m_p0 = qcr ? rot_combine(cR, a_pp, sR, a_pq, true) : a_pp;
           const dd m_p1 = qcr ? rot_combine(sR, a_pp, cR, a_pq, false) : dd_make(0.f);
           if (q < n) {
-            const dd a_qp = ldd(Ar, q * n + pc);
-            const dd a_qq = qcr ? ldd(Ar, q * n + qc) : dd_make(0.f);
+            const dd a_qp = ldx<SM>(Ar, q * n + pc);
+            const dd a_qq = qcr ? ldx<SM>(Ar, q * n + qc) : dd_make(0.f);
             const dd m_q0 = qcr ? rot_combine(cR, a_qp, sR, a_qq, true) : a_qp;
             const dd m_q1 = qcr ? rot_combine(sR, a_qp, cR, a_qq, false) : dd_make(0.f);
             // A' = J_P^T M
-            sdd(Bw, p * n + pc, rot_combine(cP, m_p0, sP, m_q0, true));
-            sdd(Bw, q * n + pc, rot_combine(sP, m_p0, cP, m_q0, false));
+            stx<SM>(Bw, p * n + pc, rot_combine(cP, m_p0, sP, m_q0, true));
+            stx<SM>(Bw, q * n + pc, rot_combine(sP, m_p0, cP, m_q0, false));
             if (qcr) {
-              sdd(Bw, p * n + qc, rot_combine(cP, m_p1, sP, m_q1, true));
-              sdd(Bw, q * n + qc, rot_combine(sP, m_p1, cP, m_q1, false));
+              stx<SM>(Bw, p * n + qc, rot_combine(cP, m_p1, sP, m_q1, true));
+              stx<SM>(Bw, q * n + qc, rot_combine(sP, m_p1, cP, m_q1, false));
             }
           } else {
-            sdd(Bw, p * n + pc, m_p0);
-            if (qcr) sdd(Bw, p * n + qc, m_p1);
+            stx<SM>(Bw, p * n + pc, m_p0);
+            if (qcr) stx<SM>(Bw, p * n + qc, m_p1);
           }
         } else if (qcr) {
           const int i = it - half;
-          const dd v0 = ldd(Vw, i * n + pc), v1 = ldd(Vw, i * n + qc);
-          sdd(Vw, i * n + pc, rot_combine(cR, v0, sR, v1, true));
-          sdd(Vw, i * n + qc, rot_combine(sR, v0, cR, v1, false));
+          const dd v0 = ldx<SM>(Vw, i * n + pc), v1 = ldx<SM>(Vw, i * n + qc);
+          stx<SM>(Vw, i * n + pc, rot_combine(cR, v0, sR, v1, true));
+          stx<SM>(Vw, i * n + qc, rot_combine(sR, v0, cR, v1, false));
         }
       }
       if (!grid_barrier(P)) return;
@@ -278,17 +306,19 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
   for (int j = blockIdx.x * JNT + threadIdx.x; j < n; j += gridDim.x * JNT) {
     dd acc = dd_make(0.0f);
     for (int i = 0; i < n; ++i) {
-      const dd v = ldd(P.V, (long)i * n + j);
+      const dd v = ldx<SM>(VV, i * n + j);
       acc = dd_add(acc, dd_mul(v, v));
     }
-    __stcg(nrm2 + j, dd_to_double(acc));
+    if (SM) nrm2[j] = dd_to_double(acc);
+    else __stcg(nrm2 + j, dd_to_double(acc));
   }
   if (!grid_barrier(P)) return;
   for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
     const int i = (int)(idx / n), j = (int)(idx % n);
-    const float2 a = __ldcg(A + idx), v = __ldcg(P.V + idx);
-    const double nj = __ldcg(nrm2 + j);
-    P.A_out[idx] = ((double)a.x + (double)a.y) / (i == j ? nj : sqrt(nj * __ldcg(nrm2 + i)));
+    const float2 a = ldx2<SM>(A, idx), v = ldx2<SM>(VV, idx);
+    const double nj = SM ? nrm2[j] : __ldcg(nrm2 + j);
+    const double ni = SM ? nrm2[i] : __ldcg(nrm2 + i);
+    P.A_out[idx] = ((double)a.x + (double)a.y) / (i == j ? nj : sqrt(nj * ni));
     P.V_out[idx] = ((double)v.x + (double)v.y) / sqrt(nj);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -374,25 +404,29 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   P.max_sweeps = max_sweeps;
   DSRG_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
   DSRG_CUDA(cudaMemsetAsync(status_dev, 0, 4 * sizeof(int), st));
-  const size_t smem = (sizeof(float4) + sizeof(int2)) * (size_t)(m / 2);
+  if ((long)n * n >= (1L << 31)) return DSRG_FNO_ERR_UNSUPPORTED;  // 32-bit element offsets
   constexpr int SMEM_CEILING = 200 * 1024;
+  // small matrices: one block with A, its copy and V in shared memory
+  const bool in_smem = n <= SMEM_JACOBI_N;
+  const size_t smem = in_smem ? sizeof(float4) * (size_t)m + 3 * sizeof(float2) * (size_t)n * n
+                              : (sizeof(float4) + sizeof(int2)) * (size_t)(m / 2);
   if (smem > (size_t)SMEM_CEILING) return DSRG_FNO_ERR_UNSUPPORTED;
   // one fixed ceiling for every launch: concurrent callers (batch workers)
   // never lower it under one another
+  auto kern = in_smem ? jacobi_coop_kernel<true> : jacobi_coop_kernel<false>;
   if (smem > 48 * 1024)
-    DSRG_CUDA(cudaFuncSetAttribute(jacobi_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CEILING));
+    DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CEILING));
   int dev = 0, sms = 0, occ = 0;
   DSRG_CUDA(cudaGetDevice(&dev));
   DSRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_coop_kernel, JNT, smem));
+  DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, JNT, smem));
   if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
   // (half + n) items of half column pairs per round; small matrices use few blocks
   const long units = (long)(m / 2 + n) * (m / 2);
-  if ((long)n * n >= (1L << 31)) return DSRG_FNO_ERR_UNSUPPORTED;  // 32-bit element offsets
   int nblk = (int)std::min<long>(std::min(sms * std::min(occ, JACOBI_BLOCKS_PER_SM), JMAX_BLOCKS), (units + 8 * JNT - 1) / (8 * JNT));
-  nblk = std::max(nblk, 1);
+  nblk = in_smem ? 1 : std::max(nblk, 1);
   void* args[] = {&P};
-  DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_coop_kernel, dim3(nblk), dim3(JNT), args, smem, st));
+  DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(JNT), args, smem, st));
   DSRG_LAUNCH_CHECK();
   int h[3] = {0, 0, 0};
   DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
