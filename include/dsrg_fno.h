@@ -93,6 +93,47 @@ int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stre
 int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
                      void* stream);
 
+/* D_vv of dsrg_fno_vv_opdm plus Eq. A12 term 13,
+ *   t^{uw}_{ez} t^{xy}_{fv} Lambda^{xyz}_{uvw},
+ * the contraction with the state-averaged 3-cumulant that Sec. 2 drops
+ * whenever the final energy drops Lambda3 (for an energy that keeps it, or to
+ * measure what dropping it does to the ONs and N').
+ *   lambda3  device [nact]^6, Lambda^{xyz}_{uvw} at
+ *            ((((x*nact + y)*nact + z)*nact + u)*nact + v)*nact + w, as written
+ *            by dsrg_fno_sa_lambda3; required when nact > 0 (NULL gives
+ *            DSRG_FNO_ERR_ARG), ignored when nact == 0; read only.
+ *   Other arguments, outputs and errors as for dsrg_fno_vv_opdm; a non-finite
+ *   lambda3 gives DSRG_FNO_ERR_NONFINITE.  The term is formed in float64 in
+ *   both precisions; with SLICED_BF16 its final contraction (length nact^3,
+ *   when >= 256) runs on the digit-plane tensor-core path like terms 10-12. */
+int dsrg_fno_vv_opdm_lambda3(const dsrg_fno_problem* prob, const double* lambda3, double* dvv_out,
+                             double* e2_out, void* stream);
+
+/* State-averaged spin-free 3-cumulant Lambda^{xyz}_{uvw} on the device (the
+ * 3-body density cumulant named after Eq. A12), from the ensemble's Gamma1
+ * and 2-cumulant and the per-state spin-free 3-RDMs.
+ *   weights        host [nstates], each >= 0, summing to 1 (1e-12); nstates <= 32.
+ *   gamma1         device [nact][nact], ensemble Gamma^u_v (as in dsrg_fno_problem).
+ *   lambda2        device [nact]^4, ensemble Lambda^{uv}_{xy} (as in dsrg_fno_problem).
+ *   gamma3_states  device [nstates][nact]^6, state a's
+ *                  Gamma3_a[x][y][z][u][v][w] = sum_{s,t,r} <a+_{xs} a+_{yt} a+_{zr} a_{wr} a_{vt} a_{us}>.
+ *   lambda3_out    device [nact]^6 (layout as in dsrg_fno_vv_opdm_lambda3).
+ * The ensemble Gamma3 = sum_a w_a Gamma3_a; the cumulant is the spin sum of
+ * the spin-orbital cumulant over the pairs (x,u), (y,v), (z,w) with the
+ * spin-orbital 1-RDM Gamma1/2 per spin (exact for spin-adapted ensembles, a
+ * definition otherwise, like Lambda2):
+ *   Lambda3 = Gamma3 - [G^x_u L^{yz}_{vw} + G^y_v L^{xz}_{uw} + G^z_w L^{xy}_{uv}]
+ *           + 1/2 [G^x_v L^{yz}_{uw} + G^x_w L^{yz}_{vu} + G^y_u L^{xz}_{vw}
+ *                  + G^y_w L^{xz}_{uv} + G^z_u L^{xy}_{wv} + G^z_v L^{xy}_{uw}]
+ *           - G^x_u G^y_v G^z_w + 1/2 [G^x_v G^y_u G^z_w + G^x_w G^y_v G^z_u + G^x_u G^y_w G^z_v]
+ *           - 1/4 [G^x_v G^y_w G^z_u + G^x_w G^y_u G^z_v].
+ * Errors: DSRG_FNO_ERR_ARG for nact outside 1..16, nstates outside 1..32, a
+ * null or host pointer where a device one is due, or bad weights;
+ * DSRG_FNO_ERR_NONFINITE for a non-finite result.  Synchronises `stream`. */
+int dsrg_fno_sa_lambda3(int32_t nact, int32_t nstates, const double* weights, const double* gamma1,
+                        const double* lambda2, const double* gamma3_states, double* lambda3_out,
+                        void* stream);
+
 /* Natural orbitals of D_vv (Eq. 8) and the truncation of Sec. 2.
  *   dvv       device [nvir][nvir], symmetric, read only.
  *   mode      0: p_o (Eq. 10, threshold in percent of the summed ONs);

@@ -111,6 +111,34 @@ def theta(prob):
     return 2.0 * np.eye(prob.nact) - prob.gamma1
 
 
+def sa_lambda3(g1, lam2, g3):
+    """Spin-free 3-cumulant Lambda^{xyz}_{uvw} = lambda3[x][y][z][u][v][w] of
+    the ensemble from its spin-free Gamma1, 2-cumulant and 3-RDM
+    Gamma3[x][y][z][u][v][w] = sum_{s,t,r} <a+_{xs} a+_{yt} a+_{zr} a_{wr} a_{vt} a_{us}>
+    (the 3-body density cumulant named after Eq. A12; R-Gamma extended).
+
+    Definition used: the spin-orbital cumulant (Gamma3 minus its antisymmetrised
+    Gamma1 x lambda2 and Gamma1 x Gamma1 x Gamma1 parts) summed over the spins
+    of the pairs (x,u), (y,v), (z,w), with the spin-orbital 1-RDM taken as
+    Gamma1 / 2 for either spin.  A Gamma1 factor that links an upper index to
+    its own lower partner keeps weight 1; one that links it to another lower
+    index ties two spins together and weighs 1/2, and the other two indices
+    then pair as the spins dictate.  The Gamma1^3 part weighs 2^(cycles - 3)
+    per permutation of the lower indices, with its sign.  Like Lambda2, it is
+    formed from the ensemble-averaged densities."""
+    G, L = g1, lam2
+    e = np.einsum
+    return (g3
+            - e("xu,yzvw->xyzuvw", G, L) - e("yv,xzuw->xyzuvw", G, L) - e("zw,xyuv->xyzuvw", G, L)
+            + 0.5 * (e("xv,yzuw->xyzuvw", G, L) + e("xw,yzvu->xyzuvw", G, L)
+                     + e("yu,xzvw->xyzuvw", G, L) + e("yw,xzuv->xyzuvw", G, L)
+                     + e("zu,xywv->xyzuvw", G, L) + e("zv,xyuw->xyzuvw", G, L))
+            - e("xu,yv,zw->xyzuvw", G, G, G)
+            + 0.5 * (e("xv,yu,zw->xyzuvw", G, G, G) + e("xw,yv,zu->xyzuvw", G, G, G)
+                     + e("xu,yw,zv->xyzuvw", G, G, G))
+            - 0.25 * (e("xv,yw,zu->xyzuvw", G, G, G) + e("xw,yu,zv->xyzuvw", G, G, G)))
+
+
 # --------------------------------------------------------------------------
 # Integrals and amplitudes (Eqs. A6, A7)
 # --------------------------------------------------------------------------
@@ -132,14 +160,16 @@ def t2_vv(prob, i, j):
     return regularizer(delta2(prob, i, j, v, v), prob.s) * nu, nu
 
 
-def t2_semi_internal(prob):
+def t2_semi_internal(prob, holes=None):
     """ts[i][j][e][x] = t^{ij}_{ex} (e virtual, x active particle), Eq. A7,
-    for every ordered hole pair (i, j)."""
+    for every ordered hole pair (i, j); `holes` (an index array) restricts
+    i and j to those holes, in that order."""
     sp = spaces(prob)
-    Bv = prob.B[:, :, sp.na:]
-    Ba = prob.B[:, :, : sp.na]
+    h = np.arange(sp.nh) if holes is None else np.asarray(holes)
+    Bv = prob.B[:, h, sp.na:]
+    Ba = prob.B[:, h, : sp.na]
     nu = np.einsum("Qie,Qjx->ijex", Bv, Ba, optimize=True)
-    eh, ep = hole_eps(prob), particle_eps(prob)
+    eh, ep = hole_eps(prob)[h], particle_eps(prob)
     d = (eh[:, None, None, None] + eh[None, :, None, None]
          - ep[sp.na:][None, None, :, None] - ep[: sp.na][None, None, None, :])
     return nu * regularizer(d, prob.s)
@@ -247,11 +277,12 @@ def mp2_closed_shell(prob):
 
 
 # --------------------------------------------------------------------------
-# D_vv (Eq. A12, terms 1-12; the Lambda3 term 13 is omitted)
+# D_vv (Eq. A12, terms 1-12; the Lambda3 term 13 only with a 3-cumulant)
 # --------------------------------------------------------------------------
-def dvv_terms(prob, terms=range(1, 13), ts=None, t1=None, core_pairs=None):
+def dvv_terms(prob, terms=range(1, 14), ts=None, t1=None, core_pairs=None, lambda3=None):
     """Returns {term number: [nvir][nvir] contribution} for Eq. A12.
-    `core_pairs` restricts term 4 to the listed unordered core pairs (m <= n)."""
+    `core_pairs` restricts term 4 to the listed unordered core pairs (m <= n).
+    Term 13 is formed only when `lambda3` ([na]^6, Lambda^{xyz}_{uvw}) is given."""
     sp = spaces(prob)
     nc, na, nv = sp.nc, sp.na, sp.nv
     out = {}
@@ -351,12 +382,20 @@ def dvv_terms(prob, terms=range(1, 13), ts=None, t1=None, core_pairs=None):
                          - np.einsum("wvey,xzfu,wz,uvxy->ef", taa, taa, G, L, optimize=True)
                          - np.einsum("vwey,zxfu,wz,uvxy->ef", taa, taa, G, L, optimize=True)
                          - np.einsum("vwex,yzfu,wz,uvxy->ef", taa, taa, G, L, optimize=True))
+    if na and lambda3 is not None and 13 in want:
+        out[13] = dvv_term13(ts[A, A], lambda3)
     return out
 
 
-def dvv(prob, return_asym=False):
-    """Symmetrised D_vv = 1/2 (D + D^T) of Eq. A12 terms 1-12."""
-    parts = dvv_terms(prob)
+def dvv_term13(taa, lambda3):
+    """Eq. A12 term 13: t^{uw}_{ez} t^{xy}_{fv} Lambda^{xyz}_{uvw}, with
+    taa[u][w][e][z] = t^{uw}_{ez} (active holes u, w; e virtual, z active)."""
+    return np.einsum("uwez,xyfv,xyzuvw->ef", taa, taa, lambda3, optimize=True)
+
+
+def dvv(prob, return_asym=False, lambda3=None):
+    """Symmetrised D_vv = 1/2 (D + D^T) of Eq. A12 terms 1-12 (13 with lambda3)."""
+    parts = dvv_terms(prob, lambda3=lambda3)
     d = sum(parts.values())
     sym = 0.5 * (d + d.T)
     if return_asym:

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libdsrg_fno.so")
 EXPORTED = (
     "dsrg_fno_pt2_energy",
     "dsrg_fno_vv_opdm",
+    "dsrg_fno_vv_opdm_lambda3",
+    "dsrg_fno_sa_lambda3",
     "dsrg_fno_truncate",
     "dsrg_fno_truncate_noalloc",
     "dsrg_fno_cut",
@@ -81,6 +83,8 @@ def load(path: str = LIB_PATH):
     P = ctypes.POINTER(CProblem)
     lib.dsrg_fno_pt2_energy.argtypes = [P, ctypes.POINTER(d), vp]
     lib.dsrg_fno_vv_opdm.argtypes = [P, vp, ctypes.POINTER(d), vp]
+    lib.dsrg_fno_vv_opdm_lambda3.argtypes = [P, vp, vp, ctypes.POINTER(d), vp]
+    lib.dsrg_fno_sa_lambda3.argtypes = [i32, i32, ctypes.POINTER(d), vp, vp, vp, vp, vp]
     lib.dsrg_fno_truncate.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_truncate_noalloc.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_cut.argtypes = [i32, vp, i32, d, d, ctypes.POINTER(i32), vp]
@@ -107,7 +111,8 @@ def load(path: str = LIB_PATH):
                                            ctypes.POINTER(d)]
     lib.dsrg_fno_launch_count.argtypes = [i32]
     lib.dsrg_fno_launch_count.restype = ctypes.c_int64
-    for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_truncate", "dsrg_fno_truncate_noalloc",
+    for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_vv_opdm_lambda3", "dsrg_fno_sa_lambda3",
+              "dsrg_fno_truncate", "dsrg_fno_truncate_noalloc",
               "dsrg_fno_cut", "dsrg_fno_discarded_correction", "dsrg_fno_sa_densities", "dsrg_fno_batch_run"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
@@ -167,6 +172,27 @@ def dsrg_fno_vv_opdm(prob: Problem, dvv_out, stream=None) -> float:
     _check("dsrg_fno_vv_opdm", load().dsrg_fno_vv_opdm(ctypes.byref(prob.c), _ptr(dvv_out), ctypes.byref(e),
                                                       _stream(stream)))
     return e.value
+
+
+def dsrg_fno_vv_opdm_lambda3(prob: Problem, lambda3, dvv_out, stream=None) -> float:
+    """D_vv with Eq. A12 term 13 (lambda3: device [nact]^6 3-cumulant)."""
+    e = ctypes.c_double()
+    _check("dsrg_fno_vv_opdm_lambda3",
+           load().dsrg_fno_vv_opdm_lambda3(ctypes.byref(prob.c), _ptr(lambda3), _ptr(dvv_out), ctypes.byref(e),
+                                           _stream(stream)))
+    return e.value
+
+
+def dsrg_fno_sa_lambda3(weights, gamma1, lambda2, gamma3_states, lambda3_out, stream=None):
+    """Ensemble spin-free 3-cumulant on the device from the ensemble Gamma1,
+    Lambda2 and the per-state 3-RDMs gamma3_states [S][n]^6 (device tensors)."""
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    n = int(gamma1.shape[0])
+    if tuple(gamma3_states.shape) != (len(w),) + (n,) * 6 or tuple(lambda3_out.shape) != (n,) * 6:
+        raise ValueError("shapes: gamma3_states [S][n]^6, lambda3_out [n]^6")
+    _check("dsrg_fno_sa_lambda3",
+           load().dsrg_fno_sa_lambda3(n, len(w), w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(gamma1),
+                                      _ptr(lambda2), _ptr(gamma3_states), _ptr(lambda3_out), _stream(stream)))
 
 
 def dsrg_fno_truncate(nvir, dvv, mode, threshold, degen_ratio, on_out, no_out, stream=None) -> int:

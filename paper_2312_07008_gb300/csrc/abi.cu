@@ -474,10 +474,12 @@ int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
 }
 
 int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
-                        cudaStream_t st) {
+                 cudaStream_t st, const double* l3) {
   int s = validate(prob);
   if (s) return s;
   if (!dvv_out || !is_device_ptr(dvv_out)) return DSRG_FNO_ERR_ARG;
+  if (prob->nact == 0) l3 = nullptr;
+  if (l3 && !is_device_ptr(l3)) return DSRG_FNO_ERR_ARG;
   const Geometry g = geometry_of(prob);
   const int ks = slices_of(prob);
   Plan P;
@@ -495,6 +497,14 @@ int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, dou
   DSRG_TRY(ws_reserve(ws, need));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
+  if (l3) {
+    const long n3 = (long)g.na * g.na * g.na;
+    int h = 0;
+    DSRG_TRY(check_finite(l3, n3 * n3, flag, st));
+    DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSRG_CUDA(cudaStreamSynchronize(st));
+    if (h) return DSRG_FNO_ERR_NONFINITE;
+  }
   PassBuffers W{};
   DSRG_TRY(carve_pass(ws, g, P, true, nsplit, ks, W, st));
   double* t1 = ws_take<double>(ws, (size_t)g.nh * g.nv);
@@ -513,7 +523,7 @@ int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, dou
   if (g.na > 0 || prob->f_hp) {
     DSRG_PHASE("phase_small_terms", st);
     DSRG_TRY(t1_amplitudes(g, g.na ? W.ts : nullptr, prob->eps, prob->f_hp, prob->gamma1, t1, st));
-    DSRG_TRY(small_terms_f64(g, g.na ? W.ts : nullptr, t1, prob->gamma1, prob->lambda2, dvv_out, work, sf, st));
+    DSRG_TRY(small_terms_f64(g, g.na ? W.ts : nullptr, t1, prob->gamma1, prob->lambda2, l3, dvv_out, work, sf, st));
   }
   DSRG_TRY(symmetrize(g.nv, dvv_out, st));
   DSRG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
@@ -696,6 +706,14 @@ int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_o
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
   return impl_vv_opdm(ws, plan_budget(ws), prob, dvv_out, e2_out, (cudaStream_t)stream);
+}
+
+int dsrg_fno_vv_opdm_lambda3(const dsrg_fno_problem* prob, const double* lambda3, double* dvv_out, double* e2_out,
+                             void* stream) {
+  if (prob && prob->nact > 0 && !lambda3) return DSRG_FNO_ERR_ARG;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  return impl_vv_opdm(ws, plan_budget(ws), prob, dvv_out, e2_out, (cudaStream_t)stream, lambda3);
 }
 
 int dsrg_fno_truncate(int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,

@@ -96,7 +96,8 @@ struct SmallFast {
 };
 constexpr int SLICED_MIN_K = 256;
 int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1,
-                    const double* l2, double* D, double* work, const SmallFast& F, cudaStream_t st);
+                    const double* l2, const double* l3, double* D, double* work, const SmallFast& F,
+                    cudaStream_t st);
 
 // Fast form: exact bf16 digit planes on tcgen05 (sliced.cu)
 int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
@@ -137,8 +138,9 @@ int check_finite(const double* x, long n, int* flag, cudaStream_t st);
 size_t device_budget(size_t held);
 void release_batch_pools();  // batch.cu
 int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* e2_out, cudaStream_t st);
+// l3: device [nact]^6 3-cumulant for Eq. A12 term 13, or null (terms 1-12 only)
 int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
-                 cudaStream_t st);
+                 cudaStream_t st, const double* l3 = nullptr);
 int impl_truncate(Workspace& ws, int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,
                   double* on_out, double* no_out, int32_t* nkept_out, cudaStream_t st);
 int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, int32_t nkept, const double* no,

@@ -1,5 +1,6 @@
-// Semi-internal and singles contributions to D_vv (Eq. A12 terms 1-3, 6, 8-12)
-// and the singles amplitudes of Eq. A6, float64.
+// Semi-internal and singles contributions to D_vv (Eq. A12 terms 1-3, 6, 8-12,
+// and term 13 when a 3-cumulant is given) and the singles amplitudes of
+// Eq. A6, float64.
 //
 // Every term is written as D_ef += coef * sum_k X[e][k] Y[f][k]: a builder
 // kernel contracts the amplitudes with the active-space densities into X and
@@ -28,6 +29,7 @@ struct SI {
   const double* pla;  // [w][e][x][u] = sum_{vy} t^{wv}_{ey} Lambda^{uv}_{xy}
   const double* plb;  // [w][e][x][u] = sum_{vy} t^{vw}_{ey} Lambda^{uv}_{xy}
   const double* plc;  // [w][e][y][u] = sum_{vx} t^{vw}_{ex} Lambda^{uv}_{xy}
+  const double* l3;   // [na]^6 Lambda^{xyz}_{uvw} (term 13), or null
   __device__ double t(int i, int j, int e, int x) const {
     return ts[(((long)i * nh + j) * nv + e) * na + x];
   }
@@ -106,7 +108,8 @@ __global__ void lambda_kernel(SI S, int variant, double* __restrict__ out) {
 }
 
 enum TermId {
-  T1_CORE = 0, T2_ACT, T3_A, T3_B, T6, T8_A, T8_B, T9_A, T9_B, T9_C, T10, T11, T12_A, T12_B, T12_C, NTERMS
+  T1_CORE = 0, T2_ACT, T3_A, T3_B, T6, T8_A, T8_B, T9_A, T9_B, T9_C, T10, T11, T12_A, T12_B, T12_C, T13,
+  NTERMS
 };
 
 __device__ __forceinline__ void unflat3(int k, int n1, int n2, int* a, int* b, int* c) {
@@ -227,6 +230,20 @@ __global__ void build_kernel(SI S, int term, int K, double* __restrict__ X, doub
       y = S.t(nc + yy, nc + z, e, u);
       break;
     }
+    case T13: {  // t^{uw}_{ez} t^{xy}_{fv} Lambda^{xyz}_{uvw} ; k = (z, u, w)
+      int z, u, w;
+      unflat3(k, na, na, &z, &u, &w);
+      x = S.t(nc + u, nc + w, e, z);
+      const long n2 = (long)na * na, n3 = n2 * na;
+      // Lambda^{xyz}_{uvw} at ((((x na + y) na + z) na + u) na + v) na + w
+      const double* l = S.l3 + ((long)z * na + u) * n2 + w;
+      for (int xx = 0; xx < na; ++xx)
+        for (int yy = 0; yy < na; ++yy) {
+          const double* lxy = l + ((long)xx * na + yy) * n3 * na;
+          for (int v = 0; v < na; ++v) y = fma(S.t(nc + xx, nc + yy, e, v), lxy[(long)v * na], y);
+        }
+      break;
+    }
   }
   X[idx] = x;
   Y[idx] = y;
@@ -248,6 +265,7 @@ static void term_shape(int term, int nc, int na, int* K, double* coef) {
     case T11: *K = na * na * na; *coef = 0.25; break;
     case T12_A: *K = na * na * na; *coef = 0.5; break;
     case T12_B: case T12_C: *K = na * na * na; *coef = -0.5; break;
+    case T13: *K = na * na * na; *coef = 1.0; break;
     default: *K = 0; *coef = 0.0;
   }
 }
@@ -270,7 +288,8 @@ size_t small_terms_work_doubles(int nc, int na, int nv) {
 
 int t1_amplitudes(const Geometry& g, const double* ts, const double* eps, const double* f_hp, const double* g1,
                   double* t1, cudaStream_t st) {
-  SI S{g.nc, g.na, g.nv, g.nh, ts, nullptr, g1, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  SI S{g.nc, g.na, g.nv, g.nh, ts, nullptr, g1, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+       nullptr};
   long n = (long)g.nh * g.nv;
   if (n == 0) return DSRG_FNO_OK;
   t1_kernel<<<ceil_div(n, 256), 256, 0, st>>>(S, g, eps, f_hp, t1);
@@ -295,12 +314,13 @@ int small_terms_kmax(int nc, int na) {
   return kmax;
 }
 
-// D += terms 1-3, 6, 8-12.  work: small_terms_work_doubles() doubles.
-// With F.ks > 0, the GEMMs with K >= SLICED_MIN_K run on the tensor cores
-// (digit planes of X and Y, exact level sums), the rest in float64.
+// D += terms 1-3, 6, 8-12, and term 13 when l3 is not null.  work:
+// small_terms_work_doubles() doubles.  With F.ks > 0, the GEMMs with
+// K >= SLICED_MIN_K run on the tensor cores (digit planes of X and Y, exact
+// level sums), the rest in float64.
 int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const double* g1, const double* l2,
-                    double* D, double* work, const SmallFast& F, cudaStream_t st) {
-  SI S{g.nc, g.na, g.nv, g.nh, ts, t1, g1, l2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+                    const double* l3, double* D, double* work, const SmallFast& F, cudaStream_t st) {
+  SI S{g.nc, g.na, g.nv, g.nh, ts, t1, g1, l2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, l3};
   if (g.na > 0) {
     // partial contractions after the X / Y area of the largest term
     const int kmax = small_terms_kmax(g.nc, g.na);
@@ -334,6 +354,7 @@ int small_terms_f64(const Geometry& g, const double* ts, const double* t1, const
   }
   for (int term = 0; term < NTERMS; ++term) {
     if (g.na == 0 && term != T1_CORE) continue;
+    if (term == T13 && !l3) continue;
     int K;
     double coef;
     term_shape(term, g.nc, g.na, &K, &coef);

@@ -2,4 +2,6 @@
 
 Holds random draws and determinant bookkeeping only; no SA-DSRG arithmetic.
 """
-from .problems import Problem, make_problem, workload, WORKLOADS, CUTS, batch_sizes, batch_problem  # noqa: F401
+from .problems import (  # noqa: F401
+    Problem, make_problem, workload, WORKLOADS, CUTS, batch_sizes, batch_problem, random_density3, random_cumulant3,
+)

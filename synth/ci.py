@@ -100,6 +100,39 @@ def spin_free_rdms(C: np.ndarray, norb: int, ta: ExcitationTable, tb: Excitation
     return g1, g2
 
 
+def spin_free_rdm3(C: np.ndarray, norb: int, ta: ExcitationTable, tb: ExcitationTable,
+                   g2: np.ndarray) -> np.ndarray:
+    """Spin-free 3-RDM of one CI vector,
+    Gamma3[p][q][r][s][t][u] = sum_{sigma tau rho} <a+_{p sigma} a+_{q tau} a+_{r rho} a_{u rho} a_{t tau} a_{s sigma}>,
+    from products of E operators:
+      E_qt E_ru       = e^{qr}_{tu} + delta_tr E_qu
+      E_ps e^{qr}_{tu} = e^{pqr}_{stu} + delta_sq e^{pr}_{tu} + delta_sr e^{pq}_{ut}
+    so Gamma3 = <E_ps E_qt E_ru> - delta_tr <E_ps E_qu> - delta_sq Gamma2[p][r][t][u]
+              - delta_sr Gamma2[p][q][u][t], with <E_ps X> = <E_sp Psi | X Psi>.
+    g2 is the same vector's Gamma2 (spin_free_rdms)."""
+    n = norb
+    X = np.empty((n, n) + C.shape)
+    for p in range(n):
+        for q in range(n):
+            X[p, q] = apply_E(C, p, q, ta, tb)
+    flat = X.reshape(n * n, -1)               # row (s, p): E_sp Psi
+    m3 = np.empty((n,) * 6)                   # m3[s][p][q][t][r][u] = <E_sp Psi | E_qt E_ru Psi>
+    for r in range(n):
+        for u in range(n):
+            Y = np.empty((n, n) + C.shape)
+            for q in range(n):
+                for t in range(n):
+                    Y[q, t] = apply_E(X[r, u], q, t, ta, tb)
+            m3[:, :, :, :, r, u] = (flat @ Y.reshape(n * n, -1).T).reshape(n, n, n, n)
+    g3 = np.einsum("spqtru->pqrstu", m3).copy()
+    gram = (flat @ flat.T).reshape(n, n, n, n)   # gram[s][p][q][u] = <E_ps E_qu>
+    eye = np.eye(n)
+    g3 -= np.einsum("tr,spqu->pqrstu", eye, gram)
+    g3 -= np.einsum("sq,prtu->pqrstu", eye, g2)
+    g3 -= np.einsum("sr,pqut->pqrstu", eye, g2)
+    return g3
+
+
 def random_ci_vectors(rng: np.random.Generator, norb: int, nstates: int,
                       ndet_sparse: int | None = None):
     """Seeded random normalised CI vectors in the Sz = 0 CAS(norb, norb) space.
@@ -143,3 +176,12 @@ def state_averaged_densities(vecs, weights, norb, ta, tb):
         g2 += w * b
     lam2 = g2 - np.einsum("pr,qs->pqrs", g1, g1) + 0.5 * np.einsum("ps,qr->pqrs", g1, g1)
     return g1, g2, lam2
+
+
+def state_gamma3(vecs, norb, ta, tb):
+    """Per-state spin-free 3-RDMs [nstates][norb]^6 (spin_free_rdm3)."""
+    out = []
+    for c in vecs:
+        _, g2 = spin_free_rdms(c, norb, ta, tb)
+        out.append(spin_free_rdm3(c, norb, ta, tb, g2))
+    return np.array(out)

@@ -129,3 +129,33 @@ def batch_problem(k: int, seed: int = 3) -> Problem:
     """Instance k of the ragged batch; its data come from seed 1000*seed + k."""
     sz = batch_sizes(seed)[k]
     return make_problem(seed=1000 * seed + k, name=f"batch{seed}_{k}", **sz)
+
+
+def _pair_symmetrised(R: np.ndarray) -> np.ndarray:
+    """Average of a [n]^6 tensor over the six simultaneous permutations of its
+    index pairs (0,3), (1,4), (2,5) and over the exchange of the upper and
+    lower triples: the symmetries of a real 3-RDM and of its cumulant."""
+    import itertools
+    out = np.zeros_like(R)
+    for perm in itertools.permutations(range(3)):
+        out += np.transpose(R, list(perm) + [3 + i for i in perm])
+    out = out + np.transpose(out, (3, 4, 5, 0, 1, 2))
+    return out / 12.0
+
+
+def random_density3(nact: int, nstates: int, seed: int, scale: float = 0.05) -> np.ndarray:
+    """[nstates][nact]^6 seeded random tensors with the symmetries of spin-free
+    3-RDMs: stand-ins for the per-state 3-RDMs of active spaces whose CI
+    3-RDM is too costly to form here (normal draws, pair-symmetrised, times
+    `scale`)."""
+    rng = np.random.default_rng(seed)
+    return np.array([scale * _pair_symmetrised(rng.standard_normal((nact,) * 6)) for _ in range(nstates)])
+
+
+def random_cumulant3(nact: int, seed: int, scale: float = 0.03) -> np.ndarray:
+    """[nact]^6 seeded random tensor with the symmetries of the spin-free
+    3-cumulant: mean |entry| about scale/4, largest about 1.4 scale, which for
+    the default matches the 3-cumulants of the random CAS(6,6) ensembles here
+    (mean 0.008, largest 0.05)."""
+    rng = np.random.default_rng(seed)
+    return scale * _pair_symmetrised(rng.standard_normal((nact,) * 6))

@@ -226,6 +226,8 @@ class TinySystem:
         self.gamma2 = np.einsum("uavbxayb->uvxy", g2r)
         l3r = lam3.reshape(na, 2, na, 2, na, 2, na, 2, na, 2, na, 2)
         self.lambda3 = np.einsum("xaybzcuavbwc->xyzuvw", l3r)
+        g3r = g3a.reshape(na, 2, na, 2, na, 2, na, 2, na, 2, na, 2)
+        self.gamma3 = np.einsum("xaybzcuavbwc->xyzuvw", g3r)
 
     # -- index maps
     def hole_spatial(self, h):

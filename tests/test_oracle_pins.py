@@ -165,10 +165,10 @@ def test_fock_space_dvv_energy_and_t1(nel_act, weights, seed):
     t1f[:, na:] = t1
     T = sysm.cluster(t1f, t2)
     brute = sysm.dvv(T - T.T)
-    terms = O.dvv_terms(prob, ts=ts, t1=t1)
-    taa = ts[nc:, nc:]
-    t13 = np.einsum("uwez,xyfv,xyzuvw->ef", taa, taa, sysm.lambda3)
-    d = sum(terms.values()) + t13
+    lam3 = O.sa_lambda3(sysm.gamma1, sysm.lambda2, sysm.gamma3)
+    terms = O.dvv_terms(prob, ts=ts, t1=t1, lambda3=lam3)
+    assert set(terms) == set(range(1, 14))
+    d = sum(terms.values())
     scale = np.max(np.abs(brute))
     assert np.max(np.abs(d - brute)) <= 1e-12 * scale
     # each amplitude class separately (no cross-class contraction survives)
@@ -176,6 +176,9 @@ def test_fock_space_dvv_energy_and_t1(nel_act, weights, seed):
     t2vv[:, :, na:, na:] = t2[:, :, na:, na:]
     Tv = sysm.cluster(None, t2vv)
     assert np.allclose(sysm.dvv(Tv - Tv.T), terms[4] + terms[5] + terms[7], rtol=0, atol=1e-12 * scale)
+    # term 13 is what the brute force adds beyond terms 1-12
+    assert np.max(np.abs(terms[13])) > 1e-6 * scale
+    assert np.max(np.abs(d - terms[13] - brute)) > 1e-6 * scale
     # E_vv
     nu_vv = np.zeros((nh, nh, nv, nv))
     for k in range(nh):
@@ -370,3 +373,83 @@ def test_generator_rdms_against_fock_space():
     assert np.max(np.abs(g2 - g2_ref)) < 1e-13
     assert abs(np.trace(g1) - norb) < 1e-13
     assert abs(np.einsum("pqpq->", g2) - norb * (norb - 1)) < 1e-12
+
+
+# ------------------------------------------------------------ 3-body cumulant
+@pytest.mark.parametrize("nel_act,seed", [(2, 7), (4, 3), (4, 9)])
+def test_sa_lambda3_is_the_spin_summed_cumulant(nel_act, seed):
+    """The spin-free 3-cumulant formula equals the spin-orbital cumulant
+    (determinant-space 3-RDM minus its antisymmetrised products) summed over
+    the spins of the pairs, for spin-adapted (singlet) ensembles."""
+    sysm = TinySystem(1, 3, 1, nel_act=nel_act, nstates=2, seed=seed, weights=(0.35, 0.65))
+    lam3 = O.sa_lambda3(sysm.gamma1, sysm.lambda2, sysm.gamma3)
+    assert np.max(np.abs(sysm.lambda3)) > 1e-3
+    assert np.max(np.abs(lam3 - sysm.lambda3)) <= 1e-13
+
+
+def _brute_spin_free_rdm3(C, norb, sa):
+    """Spin-free 3-RDM of a CI matrix C[alpha string][beta string] by
+    explicit creation/annihilation on determinants (alpha spin orbitals
+    0..norb-1, beta norb..2norb-1, creators in ascending order)."""
+    from fockspace import FockSpace, rdm_spin_orbital
+    nel = 2 * bin(int(sa[0])).count("1")
+    fs = FockSpace(norb, nel)
+    psi = np.zeros(fs.dim)
+    for ia, a in enumerate(sa):
+        for ib, b in enumerate(sa):
+            psi[fs.index[int(a) | (int(b) << norb)]] = C[ia, ib]
+    g3 = rdm_spin_orbital(fs, [psi], [1.0], list(range(2 * norb)), 3)
+    g3 = g3.reshape((2, norb) * 6)
+    return np.einsum("axbycz aubvcw->xyzuvw".replace(" ", ""), g3)
+
+
+def test_generator_gamma3_against_determinant_brute_force():
+    """The input generator's spin-free 3-RDM (E-operator products) equals the
+    determinant-space brute force for random (not spin-adapted) CI vectors."""
+    from synth import ci
+    rng = np.random.default_rng(12)
+    vecs, sa, ta, tb = ci.random_ci_vectors(rng, 4, 2)
+    for c in vecs:
+        _, g2 = ci.spin_free_rdms(c, 4, ta, tb)
+        got = ci.spin_free_rdm3(c, 4, ta, tb, g2)
+        ref = _brute_spin_free_rdm3(c, 4, sa)
+        assert np.max(np.abs(ref)) > 0.1
+        assert np.max(np.abs(got - ref)) <= 1e-13
+
+
+def test_sa_lambda3_vanishes_for_a_closed_shell_determinant():
+    """A closed-shell determinant has no cumulants: Lambda2 = Lambda3 = 0."""
+    from synth import ci
+    norb = 4
+    sa = ci.strings(norb, 2)
+    ta = ci.excitation_table(sa, norb)
+    k = 3
+    C = np.zeros((len(sa), len(sa)))
+    C[k, k] = 1.0
+    g1, g2 = ci.spin_free_rdms(C, norb, ta, ta)
+    lam2 = g2 - np.einsum("pr,qs->pqrs", g1, g1) + 0.5 * np.einsum("ps,qr->pqrs", g1, g1)
+    g3 = ci.spin_free_rdm3(C, norb, ta, ta, g2)
+    assert np.max(np.abs(g3)) > 1.0
+    assert np.max(np.abs(lam2)) <= 1e-14
+    assert np.max(np.abs(O.sa_lambda3(g1, lam2, g3))) <= 1e-13
+
+
+def test_sa_lambda3_symmetries_and_partial_trace():
+    """Lambda3 of a random ensemble keeps the pair-permutation and
+    upper/lower symmetries of Gamma3; the generator's Gamma3 obeys the
+    particle-number sum rule sum_w Gamma3[x][y][w][u][v][w] = (N - 2) Gamma2."""
+    from synth import ci
+    rng = np.random.default_rng(4)
+    n = 4
+    vecs, _, ta, tb = ci.random_ci_vectors(rng, n, 3)
+    w = np.array([0.2, 0.3, 0.5])
+    g1, g2, lam2 = ci.state_averaged_densities(vecs, w, n, ta, tb)
+    g3 = np.einsum("a,a...->...", w, ci.state_gamma3(vecs, n, ta, tb))
+    assert np.max(np.abs(np.einsum("xywuvw->xyuv", g3) - (n - 2) * g2)) <= 1e-12
+    lam3 = O.sa_lambda3(g1, lam2, g3)
+    for perm in itertools.permutations(range(3)):
+        up = "xyz"
+        lo = "uvw"
+        spec = "".join(up[i] for i in perm) + "".join(lo[i] for i in perm)
+        assert np.max(np.abs(np.einsum(f"{spec}->xyzuvw", lam3) - lam3)) <= 1e-13
+    assert np.max(np.abs(np.einsum("xyzuvw->uvwxyz", lam3) - lam3)) <= 1e-13
