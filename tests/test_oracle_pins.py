@@ -201,6 +201,42 @@ def test_fock_space_dvv_energy_and_t1(nel_act, weights, seed):
             assert abs(y - ref[m, e]) <= 1e-12 * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("nel_act,weights,seed", [(2, (0.6, 0.4), 7), (4, (0.3, 0.7), 3), (2, (0.5, 0.5), 13)])
+def test_fock_space_t1_active_holes(nel_act, weights, seed):
+    """Eq. A6 for active holes u: t^u_e / R(Delta^u_e) is the one-body part of
+    [H0, T2].  Brute force: X = [H0, T2] as a determinant-space matrix; its
+    two-body part is sum Delta^{ij}_{ab} t^{ij}_{ab} {a^{ab}_{ij}} (H0 is
+    diagonal), built with the same normal ordering and subtracted; what is left
+    is a normal-ordered one-body operator plus a constant, whose ensemble
+    projection <a+_v a_e (.)> equals sum_w X1[w][e] gamma[v][w] (e is empty),
+    so X1 follows from a linear solve with the active 1-RDM."""
+    nc, na, nv = 2, 3, 2
+    sysm = TinySystem(nc, na, nv, nel_act=nel_act, nstates=2, seed=seed, weights=weights)
+    prob = make_problem(nc, na, nv, 6, seed=21 + seed, nstates=1, s=0.6)
+    prob.gamma1, prob.lambda2 = sysm.gamma1, sysm.lambda2
+    ts = O.t2_semi_internal(prob)
+    t1 = O.t1_amplitudes(prob, ts)
+    t2 = _full_t2(prob, ts)
+    eh, ep = O.hole_eps(prob), O.particle_eps(prob)
+    delta = (ep[None, None, :, None] + ep[None, None, None, :]
+             - eh[:, None, None, None] - eh[None, :, None, None])
+    T2 = sysm.cluster(None, t2)
+    H0 = sysm.h0(prob.eps)
+    R = (H0 @ T2 - T2 @ H0) - sysm.cluster(None, delta * t2)
+    base = nc + na
+    y = np.zeros((na, nv))
+    for v in range(na):
+        for e in range(nv):
+            op = sysm.fs.e1(so(nc + v, 0), so(base + e, 0))
+            y[v, e] = sysm.expect(lambda psi: op @ (R @ psi))
+    act_a = [so(nc + u, 0) for u in range(na)]
+    g_aa = sysm.g1so[np.ix_(act_a, act_a)]
+    x1 = np.linalg.solve(g_aa, y)
+    ref = t1[nc:] / O.regularizer(eh[nc:, None] - ep[na:][None, :], prob.s)
+    assert np.max(np.abs(ref)) > 1e-4
+    assert np.max(np.abs(x1 - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
 def test_fock_space_sr_number_conservation():
     """Single reference: the trace of the core block of Gamma^(2) (brute force)
     cancels the trace of the oracle's D_vv; the vv block is PSD."""
