@@ -49,9 +49,12 @@ typedef enum {
 /* Arithmetic of the integral contractions.  FP64: plain float64 on the CUDA
  * cores.  SLICED_BF16: each float64 row is split into `nslices` exact bfloat16
  * digit planes with a per-row power-of-two scale; digit products run on the
- * tensor cores (tcgen05) with exact float32 partial sums and float64
- * accumulation (regulariser, energy, D_vv accumulation and eigensolve stay
- * float64). */
+ * tensor cores (tcgen05) with exact float32 level sums, merged into
+ * double-float accumulators (float32 hi + lo pairs, about 48 bits); the
+ * regulariser and the dressing of this form run in double-float, the energy
+ * and D_vv sums in float64.  In both forms the NO eigensolve runs in
+ * double-float.  On the workloads here the two forms agree to a few 1e-9 E_h
+ * in energies; ONs are tested to agree within 1e-8. */
 typedef enum { DSRG_FNO_FP64 = 0, DSRG_FNO_SLICED_BF16 = 1 } dsrg_fno_precision;
 
 typedef struct {
@@ -78,7 +81,8 @@ typedef struct {
   /* flow parameter s (E_h^-2), s >= 0 (Eq. A7). */
   double s;
   int32_t precision;  /* dsrg_fno_precision */
-  int32_t nslices;    /* SLICED_BF16 digit planes (2..8); 0 = library default */
+  int32_t nslices;    /* SLICED_BF16 digit planes: 3, 4 or 5; 0 = library default (5);
+                       * other values give DSRG_FNO_ERR_UNSUPPORTED */
 } dsrg_fno_problem;
 
 /* vv-class SA-DSRG-PT2 energy E_vv (doubles whose particles are both
@@ -217,7 +221,8 @@ typedef struct {
   /* device [nvir][nvir]: D_vv (dsrg_fno_vv_opdm); NULL = energy only */
   double* dvv_out;
   /* natural orbitals and cut (dsrg_fno_truncate): cut_mode -1 = none, else
-   * 0/1/2 with cut_threshold and cut_degen_ratio; needs dvv_out, on_out
+   * 0..3 (the modes of dsrg_fno_truncate) with cut_threshold and
+   * cut_degen_ratio; needs dvv_out, on_out
    * (device [nvir]) and no_out (device [nvir][nvir]). */
   int32_t cut_mode;
   double cut_threshold, cut_degen_ratio;
