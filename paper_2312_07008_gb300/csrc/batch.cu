@@ -147,6 +147,7 @@ extern "C" int dsrg_fno_batch_run(dsrg_fno_batch_item* items, int32_t n, int32_t
   std::vector<int> status(n, DSRG_FNO_OK);
   auto body = [&](int k) {
     cudaSetDevice(dev);
+    SharedDeviceScope shared(workers > 1);
     Worker& w = pool.w[k];
     for (;;) {
       const int j = next.fetch_add(1);

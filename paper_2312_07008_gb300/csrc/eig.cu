@@ -381,6 +381,11 @@ __global__ void eig_permute_kernel(int n, const double* __restrict__ A, const do
 
 }  // namespace
 
+static thread_local bool t_device_shared = false;
+
+SharedDeviceScope::SharedDeviceScope(bool shared) : prev(t_device_shared) { t_device_shared = shared; }
+SharedDeviceScope::~SharedDeviceScope() { t_device_shared = prev; }
+
 // A (n x n, symmetric) is destroyed: on return its diagonal holds the
 // eigenvalues; V (n x n) receives the eigenvectors (column j <-> A[j][j]).
 // work: eig_work_doubles(n) doubles.  status_dev: four ints of device memory.
@@ -421,9 +426,18 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   DSRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, JNT, smem));
   if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
-  // (half + n) items of half column pairs per round; small matrices use few blocks
+  // (half + n) items of half column pairs per round, about two per thread
+  // on a device of its own: a round's tasks are chains of dependent L2 round
+  // trips, so short chains over more blocks beat the extra grid-barrier
+  // arrivals (GB300, random spectra: n = 200 31.7 -> 17.8 ms, n = 400 65 ->
+  // 43 ms against eight per thread; n >= ~1100 is capped by the co-resident
+  // grid either way).  On a shared device, eight per thread: there the extra
+  // resident blocks cost the other workers more than they save (64-instance
+  // batch 3.30 -> 3.67 s with two per thread).
   const long units = (long)(m / 2 + n) * (m / 2);
-  int nblk = (int)std::min<long>(std::min(sms * std::min(occ, JACOBI_BLOCKS_PER_SM), JMAX_BLOCKS), (units + 8 * JNT - 1) / (8 * JNT));
+  const long per_block = (t_device_shared ? 8 : 2) * (long)JNT;
+  int nblk = (int)std::min<long>(std::min(sms * std::min(occ, JACOBI_BLOCKS_PER_SM), JMAX_BLOCKS),
+                                 (units + per_block - 1) / per_block);
   nblk = in_smem ? 1 : std::max(nblk, 1);
   void* args[] = {&P};
   DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(JNT), args, smem, st));

@@ -73,6 +73,15 @@ constexpr int EIG_MAX_BLOCKS = 1024;  // grid bound of the eigensolver (reductio
 constexpr size_t eig_work_doubles(int n) { return 3 * (size_t)n * n + 2 * EIG_MAX_BLOCKS + 16; }
 int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
                    cudaStream_t st);
+// Marks the calling thread, for the scope's lifetime, as one of several host
+// threads that share the device (batch workers): the eigensolver then keeps
+// its cooperative grid small, since its blocks stay resident through every
+// grid barrier and would crowd out the other workers' kernels.
+struct SharedDeviceScope {
+  bool prev;
+  explicit SharedDeviceScope(bool shared);
+  ~SharedDeviceScope();
+};
 int eig_sort(int n, const double* A, const double* V, double* evals, double* evecs, int* rank,
              bool descending, bool fix_sign, cudaStream_t st);
 
