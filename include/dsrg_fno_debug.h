@@ -36,6 +36,13 @@ int dsrg_fno_debug_slice_rows_dd(int32_t nslices, int32_t R, int32_t K, const fl
  * float64 (the double-float value rounded). */
 int dsrg_fno_debug_regularizer(int32_t n, const double* delta, double s, double* r1, double* y);
 
+/* The stacked-B issue schedule of the digit-plane MMAs for nslices planes
+ * (3..6), host only: entries[5*i ..] = {A plane, first B plane, B planes,
+ * first level, N columns} of the i-th MMA of a 16-wide k step, in issue
+ * order.  Returns the number of MMAs (>= 0), or DSRG_FNO_ERR_ARG for a bad
+ * nslices, a null pointer or max_entries below that number. */
+int dsrg_fno_debug_mma_schedule(int32_t nslices, int32_t* entries, int32_t max_entries);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,7 @@ EXPORTED = (
     "dsrg_fno_debug_slice_rows",
     "dsrg_fno_debug_slice_rows_dd",
     "dsrg_fno_debug_regularizer",
+    "dsrg_fno_debug_mma_schedule",
     "dsrg_fno_profile_enable",
     "dsrg_fno_profile_query",
     "dsrg_fno_launch_count",
@@ -105,6 +106,8 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_debug_slice_rows_dd.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_float),
                                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
     lib.dsrg_fno_debug_regularizer.argtypes = [i32, dp, d, dp, dp]
+    lib.dsrg_fno_debug_mma_schedule.argtypes = [i32, ctypes.POINTER(i32), i32]
+    lib.dsrg_fno_debug_mma_schedule.restype = ctypes.c_int
     lib.dsrg_fno_profile_enable.argtypes = [i32]
     lib.dsrg_fno_profile_enable.restype = None
     lib.dsrg_fno_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
@@ -297,3 +300,12 @@ def dsrg_fno_profile_query(name: str):
 
 def dsrg_fno_launch_count(reset: bool = False) -> int:
     return load().dsrg_fno_launch_count(1 if reset else 0)
+
+
+def dsrg_fno_debug_mma_schedule(nslices: int):
+    """Stacked-B MMA issue schedule of one k step (host only): a list of
+    (A plane, first B plane, B planes, first level, N columns)."""
+    buf = (ctypes.c_int32 * (5 * 64))()
+    n = load().dsrg_fno_debug_mma_schedule(int(nslices), buf, 64)
+    _check("dsrg_fno_debug_mma_schedule", min(n, 0))
+    return [tuple(buf[5 * i:5 * i + 5]) for i in range(n)]

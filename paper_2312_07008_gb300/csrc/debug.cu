@@ -5,6 +5,7 @@
 
 #include "../../include/dsrg_fno_debug.h"
 #include "kernels.h"
+#include "mma_schedule.cuh"
 
 using namespace dsrg;
 
@@ -93,4 +94,19 @@ extern "C" int dsrg_fno_debug_regularizer(int32_t n, const double* delta, double
   DSRG_CUDA(cudaMemcpy(r1, a.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
   DSRG_CUDA(cudaMemcpy(y, b.p, sizeof(double) * n, cudaMemcpyDeviceToHost));
   return DSRG_FNO_OK;
+}
+
+extern "C" int dsrg_fno_debug_mma_schedule(int32_t ks, int32_t* entries, int32_t max_entries) {
+  if (ks < 3 || ks > 6 || !entries) return DSRG_FNO_ERR_ARG;
+  const int n = stacked_mma_count(ks);
+  if (max_entries < n) return DSRG_FNO_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    const StackedMma m = stacked_mma(ks, i);
+    entries[5 * i + 0] = m.a;
+    entries[5 * i + 1] = m.b0;
+    entries[5 * i + 2] = m.nb;
+    entries[5 * i + 3] = m.level;
+    entries[5 * i + 4] = m.nb * plane_tile_n(ks);
+  }
+  return n;
 }
