@@ -186,6 +186,24 @@ def batch_cpu_baseline(seconds):
     return r
 
 
+def single_config(p, name, cuts, nslices):
+    """`config` of a single-workload line (both arms)."""
+    return {"workload": name, "ncore": p.ncore, "nact": p.nact, "nvir": p.nvir, "naux": p.naux,
+            "nstates": len(p.weights), "s": p.s, "cuts_po": list(cuts), "nslices": nslices,
+            "l2": f"inputs larger than L2 (B = {p.B.nbytes / 1e9:.2f} GB)", "parallelism": "replicas"}
+
+
+def batch_config(nslices):
+    """`config` of a batch line (both arms): the shape recipe of the 64 instances."""
+    from synth.problems import batch_sizes
+    sizes = batch_sizes()
+    bbytes = sum(8 * s["naux"] * (s["ncore"] + s["nact"]) * (s["nact"] + s["nvir"]) for s in sizes)
+    return {"workload": BATCH_WORKLOAD, "instances": len(sizes), "ncore": "U{10..60}", "nact": "{0,4,6,8}",
+            "nvir": "U{100..800}", "naux": "3 (ncore+nact+nvir)", "nstates": "2..5",
+            "cut_po": BATCH_CUT, "nslices": nslices,
+            "l2": f"inputs larger than L2 ({bbytes / 1e9:.1f} GB of B)", "parallelism": "replicas"}
+
+
 def reference_arm(args):
     from synth import workload
     rank = int(os.environ.get("RANK", "0"))
@@ -194,9 +212,11 @@ def reference_arm(args):
     batch = args.workload == BATCH_WORKLOAD
     if batch:
         base = lambda sec: batch_cpu_baseline(sec)  # noqa: E731
+        config = batch_config(args.nslices)
     else:
         p = workload(args.workload)
         base = lambda sec: cpu_baseline(p, sec)  # noqa: E731
+        config = single_config(p, args.workload, cuts_of(args.workload), args.nslices)
     vals = []
     for _ in range(args.warmup):
         base(max(2.0, args.cpu_seconds / 4))
@@ -207,7 +227,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload},
+            "config": config,
             "cpu_baseline": {"value": v, "unit": unit, "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -351,9 +371,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"bf16 digit planes (k={args.nslices}) -> exact f32 level sums -> f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "ncore": p.ncore, "nact": p.nact, "nvir": p.nvir, "naux": p.naux,
-                   "nstates": len(p.weights), "s": p.s, "cuts_po": list(cuts), "nslices": args.nslices,
-                   "l2": f"inputs larger than L2 (B = {p.B.nbytes / 1e9:.2f} GB)", "parallelism": "replicas"},
+        "config": single_config(p, args.workload, cuts, args.nslices),
         "gflops": flops * value / 1e9,
         "s_per_solve": ms_max / args.steps / 1e3,
         "roofline": roofline,
@@ -556,11 +574,8 @@ def batch_arm(args):
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"bf16 digit planes (k={args.nslices}) -> exact f32 level sums -> f64",
         "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD, "instances": n, "ncore": "U{10..60}", "nact": "{0,4,6,8}",
-                   "nvir": "U{100..800}", "naux": "3 (ncore+nact+nvir)", "nstates": "2..5",
-                   "cut_po": BATCH_CUT, "nslices": args.nslices, "workers": workers,
-                   "l2": f"inputs larger than L2 ({sum(p.B.nbytes for p in probs) / 1e9:.1f} GB of B)",
-                   "parallelism": "replicas"},
+        "config": batch_config(args.nslices),
+        "workers": workers,
         "gflops": flops * value / n / 1e9,
         "s_per_step": ms_max / args.steps / 1e3,
         "roofline": roofline,
