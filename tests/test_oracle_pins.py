@@ -148,13 +148,14 @@ def _full_t2(prob, ts):
     return t2
 
 
-@pytest.mark.parametrize("nel_act,weights,seed", [(2, (0.6, 0.4), 7), (4, (0.3, 0.7), 3)])
+@pytest.mark.parametrize("nel_act,weights,seed", [(2, (0.6, 0.4), 7), (4, (0.3, 0.7), 3),
+                                                   (4, (0.2, 0.3, 0.5), 17)])
 def test_fock_space_dvv_energy_and_t1(nel_act, weights, seed):
     """Eq. A12 terms 1-12 (+ the Lambda3 term 13, formed here from the CI),
     E_vv, and the one-body part of [H0, T2] in Eq. A6, all against explicit
     determinant-space evaluation with spin-adapted (singlet) ensembles."""
     nc, na, nv = 2, 3, 2
-    sysm = TinySystem(nc, na, nv, nel_act=nel_act, nstates=2, seed=seed, weights=weights)
+    sysm = TinySystem(nc, na, nv, nel_act=nel_act, nstates=len(weights), seed=seed, weights=weights)
     prob = make_problem(nc, na, nv, 6, seed=11 + seed, nstates=1, s=0.7)
     prob.gamma1, prob.lambda2 = sysm.gamma1, sysm.lambda2
     nh, npart = nc + na, na + nv
