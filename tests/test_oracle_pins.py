@@ -373,6 +373,43 @@ def test_correction_limits():
     assert abs(efno5) < abs(e)
 
 
+def test_correction_is_basis_free_inside_the_kept_space():
+    """Recanonicalisation (Sec. 2) makes E_vv(FNO) a function of the kept
+    space alone: any orthonormal basis of it gives the same energy and the
+    same recanonicalised orbital energies."""
+    prob = make_problem(ncore=3, nact=2, nvir=12, naux=15, seed=18, nstates=2, s=0.5)
+    n, v = O.natural_orbitals(O.dvv(prob))
+    k = 6
+    de, efno, eps = O.discarded_correction(prob, v, k)
+    q, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((k, k)))
+    v2 = v.copy()
+    v2[:, :k] = v[:, :k] @ q
+    de2, efno2, eps2 = O.discarded_correction(prob, v2, k)
+    assert abs(efno2 - efno) <= 1e-12 * abs(efno)
+    assert np.max(np.abs(eps2 - eps)) <= 1e-13
+
+
+def test_correction_on_a_subset_of_canonical_virtuals():
+    """Kept space = a subset S of the semicanonical virtuals: E_vv(FNO) is
+    E_vv of the problem whose virtual space is S, built by slicing B and eps."""
+    prob = make_problem(ncore=3, nact=2, nvir=12, naux=15, seed=19, nstates=2, s=0.5)
+    S = [7, 2, 10, 4, 0]
+    no = np.zeros((12, 12))
+    for c, e in enumerate(S):
+        no[e, c] = 1.0
+    _, efno, eps = O.discarded_correction(prob, no, len(S))
+    from copy import copy
+    sub = copy(prob)
+    keep = sorted(S)
+    na = prob.nact
+    sub.B = np.ascontiguousarray(np.concatenate([prob.B[:, :, :na], prob.B[:, :, [na + e for e in keep]]], axis=2))
+    sub.nvir = len(keep)
+    nh = prob.ncore + prob.nact
+    sub.eps = np.concatenate([prob.eps[:nh], prob.eps[nh:][keep]])
+    assert np.allclose(eps, prob.eps[nh:][keep], rtol=0, atol=1e-15)
+    assert abs(efno - O.e_vv(sub)) <= 1e-12 * abs(efno)
+
+
 # ------------------------------------------------------------- generator RDMs
 def test_generator_rdms_against_fock_space():
     """synth.ci spin-free RDMs of a random CI vector agree with the
