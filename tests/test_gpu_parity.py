@@ -113,6 +113,22 @@ def test_truncation_modes_match_oracle():
             assert k == O.truncate(n_ref, mode, thr, ratio), (mode, thr, ratio)
 
 
+def test_cut_matches_truncate_in_every_mode():
+    """dsrg_fno_cut on the ONs dsrg_fno_truncate wrote gives the same N' as a
+    fresh truncation, for every mode, threshold and widening ratio."""
+    p = make_problem(ncore=4, nact=2, nvir=60, naux=50, seed=35, nstates=2)
+    ref_d = O.dvv(p)
+    n_ref, _ = O.natural_orbitals(ref_d)
+    d = torch.from_numpy(ref_d).cuda()
+    on = torch.empty(60, dtype=torch.float64, device="cuda")
+    no = torch.empty((60, 60), dtype=torch.float64, device="cuda")
+    pkg.dsrg_fno_truncate(60, d, 0, 98.0, 0.01, on, no)
+    for mode, thr in ((0, 95.0), (0, 100.0), (1, 25.0), (1, 100.0), (2, 1e-3), (2, 1e3), (3, 17.0), (3, 60.0)):
+        for ratio in (0.01, 0.0, 0.5):
+            k = pkg.dsrg_fno_cut(60, on, mode, thr, ratio)
+            assert k == O.truncate(n_ref, mode, thr, ratio), (mode, thr, ratio)
+
+
 def test_invalid_arguments_are_rejected():
     p = make_problem(ncore=2, nact=2, nvir=10, naux=8, seed=36, nstates=2)
     gp = pkg.problem_from_synth(p)
