@@ -283,6 +283,28 @@ def test_vv_terms_match_hole_rdm_form():
     assert np.max(np.abs(d - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
+def test_sr_term4_symmetric_output_form():
+    """Single reference: term 4 of Eq. A12 equals
+    2 [sum_{m<n} (1/2 P + 3/2 M) + sum_m A_m A_m^T] with A = t^{mn} as an
+    (e, e') matrix, P = (A + A^T)(A + A^T)^T and M = (A - A^T)(A - A^T)^T, the
+    symmetric (A + A^T) / (A - A^T) split the core-pair dressing uses; hence
+    D_vv is positive semidefinite."""
+    prob = make_problem(ncore=4, nact=0, nvir=9, naux=13, seed=23, s=0.5)
+    t4 = O.dvv_terms(prob, terms=(4,))[4]
+    ref = np.zeros((9, 9))
+    for m in range(4):
+        for n in range(m, 4):
+            A = O.t2_vv(prob, m, n)[0]
+            if m == n:
+                ref += 2.0 * A @ A.T
+            else:
+                P = (A + A.T) @ (A + A.T).T
+                M = (A - A.T) @ (A - A.T).T
+                ref += 2.0 * (0.5 * P + 1.5 * M)
+    assert np.max(np.abs(t4 - ref)) <= 1e-13 * np.max(np.abs(ref))
+    assert np.linalg.eigvalsh(0.5 * (t4 + t4.T)).min() >= -1e-14 * np.max(np.abs(t4))
+
+
 def test_dvv_symmetric_and_invariant_under_aux_rotation():
     prob = make_problem(ncore=3, nact=2, nvir=6, naux=9, seed=12, nstates=2, s=0.5)
     d, asym = O.dvv(prob, return_asym=True)
