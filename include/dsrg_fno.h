@@ -174,9 +174,13 @@ int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold
  * scratch is one fixed file-scope device array of the library (5 nvir^2
  * doubles and a few KB for nvir up to 512, about 10.5 MB), held by every device that loads
  * the library until the process exits.
- *   - nvir > 512 returns DSRG_FNO_ERR_ARG (message on stderr).
- *   - The first call on a device looks up the array's device address on that
- *     device (set-up); make that first call before any stream capture.
+ *   - nvir > 512 returns DSRG_FNO_ERR_ARG, with the limit named in a message
+ *     to the log callback (dsrg_fno_set_log_callback).  dvv, on_out and
+ *     no_out must be device memory (else DSRG_FNO_ERR_ARG, before any work).
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ *     device also loads the library's device code there (set-up), so make
+ *     that first call before any stream capture.
  *   - Every call on a device shares the array, which keeps the last call's
  *     contents; each call writes every scratch word before reading it.  Calls
  *     whose GPU work overlaps (other streams or threads) race on the array:
@@ -255,6 +259,16 @@ const char* dsrg_fno_status_string(int status);
 
 /* Frees the device workspace of every device the library touched. */
 void dsrg_fno_release(void);
+
+/* Log sink of the library (the paper has no counterpart).  The library
+ * writes nothing to stdout or stderr; the text of a failed CUDA call or of a
+ * rejected argument goes to `fn` (level 0 error, 1 warning; `message` is
+ * valid during the call only), with `user` passed through.  NULL (the
+ * default) drops the messages; the status codes are returned either way.
+ * The callback may be called from any thread that calls the library, one
+ * message at a time. */
+typedef void (*dsrg_fno_log_fn)(int level, const char* message, void* user);
+void dsrg_fno_set_log_callback(dsrg_fno_log_fn fn, void* user);
 
 #ifdef __cplusplus
 }

@@ -43,6 +43,11 @@ int dsrg_fno_debug_regularizer(int32_t n, const double* delta, double s, double*
  * nslices, a null pointer or max_entries below that number. */
 int dsrg_fno_debug_mma_schedule(int32_t nslices, int32_t* entries, int32_t max_entries);
 
+/* Bytes of device workspace the single-instance calls hold on the current
+ * device (grow-only; 0 before the first call and after dsrg_fno_release()).
+ * Host only: reads the library's bookkeeping, launches nothing. */
+int64_t dsrg_fno_debug_workspace_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -262,20 +262,6 @@ def e_vv(prob, components=None):
     return total
 
 
-def mp2_closed_shell(prob):
-    """Closed-shell MP2 energy sum_{mnef} nu(2 nu - nu_swap)/Delta (no active)."""
-    tot = 0.0
-    nc = prob.ncore
-    for m in range(nc):
-        for n in range(nc):
-            nu = nu_pair(prob, m, n, slice(prob.nact, None), slice(prob.nact, None))
-            nus = nu_pair(prob, n, m, slice(prob.nact, None), slice(prob.nact, None))
-            v = np.arange(prob.nact, prob.nact + prob.nvir)
-            d = delta2(prob, m, n, v, v)
-            tot += np.sum(nu * (2 * nu - nus) / d)
-    return tot
-
-
 # --------------------------------------------------------------------------
 # D_vv (Eq. A12, terms 1-12; the Lambda3 term 13 only with a 3-cumulant)
 # --------------------------------------------------------------------------

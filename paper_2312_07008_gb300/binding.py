@@ -33,6 +33,8 @@ EXPORTED = (
     "dsrg_fno_debug_slice_rows_dd",
     "dsrg_fno_debug_regularizer",
     "dsrg_fno_debug_mma_schedule",
+    "dsrg_fno_debug_workspace_bytes",
+    "dsrg_fno_set_log_callback",
     "dsrg_fno_profile_enable",
     "dsrg_fno_profile_query",
     "dsrg_fno_launch_count",
@@ -70,6 +72,9 @@ class CBatchItem(ctypes.Structure):
 
 
 _lib = None
+# void (*)(int level, const char* message, void* user)
+LOG_FN = ctypes.CFUNCTYPE(None, ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p)
+_log_keep = None  # the installed ctypes callback, kept alive while installed
 
 
 def load(path: str = LIB_PATH):
@@ -108,6 +113,10 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_debug_regularizer.argtypes = [i32, dp, d, dp, dp]
     lib.dsrg_fno_debug_mma_schedule.argtypes = [i32, ctypes.POINTER(i32), i32]
     lib.dsrg_fno_debug_mma_schedule.restype = ctypes.c_int
+    lib.dsrg_fno_debug_workspace_bytes.argtypes = []
+    lib.dsrg_fno_debug_workspace_bytes.restype = ctypes.c_int64
+    lib.dsrg_fno_set_log_callback.argtypes = [LOG_FN, vp]
+    lib.dsrg_fno_set_log_callback.restype = None
     lib.dsrg_fno_profile_enable.argtypes = [i32]
     lib.dsrg_fno_profile_enable.restype = None
     lib.dsrg_fno_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64),
@@ -309,3 +318,21 @@ def dsrg_fno_debug_mma_schedule(nslices: int):
     n = load().dsrg_fno_debug_mma_schedule(int(nslices), buf, 64)
     _check("dsrg_fno_debug_mma_schedule", min(n, 0))
     return [tuple(buf[5 * i:5 * i + 5]) for i in range(n)]
+
+
+def dsrg_fno_debug_workspace_bytes() -> int:
+    """Device workspace bytes the library holds on the current device."""
+    return load().dsrg_fno_debug_workspace_bytes()
+
+
+def dsrg_fno_set_log_callback(fn=None):
+    """Routes the library's messages to fn(level, text); None drops them."""
+    global _log_keep
+    lib = load()
+    if fn is None:
+        lib.dsrg_fno_set_log_callback(LOG_FN(), None)
+        _log_keep = None
+        return
+    cb = LOG_FN(lambda level, msg, user: fn(int(level), msg.decode(errors="replace")))
+    lib.dsrg_fno_set_log_callback(cb, None)
+    _log_keep = cb

@@ -125,7 +125,7 @@ static void build_plan(int nc, int na, long cap_pairs, Plan& P) {
 // ---------------------------------------------------------------------------
 // Argument checks
 // ---------------------------------------------------------------------------
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();

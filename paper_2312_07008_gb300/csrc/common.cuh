@@ -13,12 +13,17 @@
 namespace dsrg {
 
 // Status propagation inside the library (never across the ABI as exceptions).
+// Messages go to the caller's log callback (dsrg_fno_set_log_callback);
+// without one the library prints nothing.
+void log_message(int level, const char* fmt, ...);
+constexpr int LOG_ERROR = 0, LOG_WARNING = 1;
+
 #define DSRG_CUDA(call)                                                       \
   do {                                                                        \
     cudaError_t e_ = (call);                                                  \
     if (e_ != cudaSuccess) {                                                  \
-      fprintf(stderr, "dsrg_fno: %s failed: %s (%s:%d)\n", #call,             \
-              cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+      log_message(LOG_ERROR, "%s failed: %s (%s:%d)", #call,                  \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                \
       return DSRG_FNO_ERR_CUDA;                                               \
     }                                                                         \
   } while (0)

@@ -110,3 +110,8 @@ extern "C" int dsrg_fno_debug_mma_schedule(int32_t ks, int32_t* entries, int32_t
   }
   return n;
 }
+
+extern "C" int64_t dsrg_fno_debug_workspace_bytes(void) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  return (int64_t)workspace_for_current_device().cap;
+}

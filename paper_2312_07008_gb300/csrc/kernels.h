@@ -140,6 +140,8 @@ int scale_rows(int nv, int ncol, long ld, const double* ev, const double* V, dou
                cudaStream_t st);
 int copy_active(long rows, int na, int np, int npf, const double* B, double* Bf, cudaStream_t st);
 int check_finite(const double* x, long n, int* flag, cudaStream_t st);
+// Whether p is device (or managed) memory; cudaPointerGetAttributes allocates nothing.
+bool is_device_ptr(const void* p);
 
 // Single-instance pipeline stages on an explicit workspace (abi.cu); the C
 // entry points call them on the per-device workspace, the batch runner on

@@ -6,10 +6,6 @@
 // is not acceptable.  dsrg_fno_truncate_noalloc serves them with the same
 // eigensolver and cut as dsrg_fno_truncate, using as scratch one file-scope
 // device array of fixed size instead of the library's workspace.
-#include <stdio.h>
-
-#include <mutex>
-
 #include "kernels.h"
 
 namespace dsrg {
@@ -23,26 +19,18 @@ constexpr size_t NOALLOC_DOUBLES = 2 * (size_t)NOALLOC_NVIR_MAX * NOALLOC_NVIR_M
 // Held by every device that loads the library, until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
-static std::mutex g_noalloc_setup_mutex;
-static double* g_noalloc_ptr[64] = {};
-
 // Device address of the array on the current device (host code cannot use
-// the symbol itself: it names a host-side stand-in).
+// the symbol itself: it names a host-side stand-in).  Looked up on every call,
+// so a device reset by the host application cannot leave a stale address.
 static int noalloc_scratch(double** out) {
-  int dev = 0;
-  DSRG_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return DSRG_FNO_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_noalloc_setup_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      fprintf(stderr, "dsrg_fno_truncate_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-      return DSRG_FNO_ERR_CUDA;
-    }
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    log_message(LOG_ERROR, "dsrg_fno_truncate_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return DSRG_FNO_ERR_CUDA;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = static_cast<double*>(p);
   return DSRG_FNO_OK;
 }
 
@@ -54,12 +42,16 @@ extern "C" int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_
                                          double degen_ratio, double* on_out, double* no_out, int32_t* nkept_out,
                                          void* stream) {
   if (nvir > NOALLOC_NVIR_MAX) {
-    fprintf(stderr, "dsrg_fno_truncate_noalloc: nvir = %d exceeds the fixed scratch limit of %d\n", nvir,
-            NOALLOC_NVIR_MAX);
+    log_message(LOG_ERROR, "dsrg_fno_truncate_noalloc: nvir = %d exceeds the fixed scratch limit of %d", nvir,
+                NOALLOC_NVIR_MAX);
     return DSRG_FNO_ERR_ARG;
   }
   if (nvir <= 0 || !dvv || !on_out || !no_out || !nkept_out) return DSRG_FNO_ERR_ARG;
   if (mode < 0 || mode > 3 || !isfinite(threshold) || !(degen_ratio >= 0.0)) return DSRG_FNO_ERR_ARG;
+  if (!is_device_ptr(dvv) || !is_device_ptr(on_out) || !is_device_ptr(no_out)) {
+    log_message(LOG_ERROR, "dsrg_fno_truncate_noalloc: dvv, on_out and no_out must be device memory");
+    return DSRG_FNO_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   double* base = nullptr;
   DSRG_TRY(noalloc_scratch(&base));

@@ -1,4 +1,6 @@
-// Launch accounting (include/dsrg_fno_profile.h).
+// Launch accounting (include/dsrg_fno_profile.h) and the log callback.
+#include <stdarg.h>
+
 #include <atomic>
 #include <string>
 #include <vector>
@@ -27,6 +29,22 @@ static std::vector<ProfRec> g_recs;
 // pairs of earlier ones and creates only what it lacks.
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_event_pool;
 static std::mutex g_prof_mutex;
+
+// The caller's log sink; messages are dropped while none is set.
+static std::mutex g_log_mutex;
+static dsrg_fno_log_fn g_log_fn = nullptr;
+static void* g_log_user = nullptr;
+
+void log_message(int level, const char* fmt, ...) {
+  std::lock_guard<std::mutex> lk(g_log_mutex);
+  if (!g_log_fn) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_log_fn(level, buf, g_log_user);
+}
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -68,6 +86,12 @@ void prof_end(void* token, cudaStream_t st) {
 }  // namespace dsrg
 
 using namespace dsrg;
+
+extern "C" void dsrg_fno_set_log_callback(dsrg_fno_log_fn fn, void* user) {
+  std::lock_guard<std::mutex> lk(g_log_mutex);
+  g_log_fn = fn;
+  g_log_user = user;
+}
 
 extern "C" void dsrg_fno_profile_enable(int32_t enable) {
   std::lock_guard<std::mutex> lk(g_prof_mutex);

@@ -44,13 +44,6 @@ constexpr int ROW_BYTES = 2 * BKE;
 constexpr int KCHUNK_BLOCKS = 320 / BKE;  // 320 k-values per exact sum of levels 0, 1, 2
 constexpr int NEXACT = 3;          // levels kept exact per chunk
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
-// CTAs per cluster sharing the A tile by TMA multicast (1, 2 or 4).  On the
-// pair contraction of the nvir 1200 / naux 3600 workload, 2 was no faster
-// than 1 (the tensor-core shared-memory path binds, not L2 -> SM traffic), so
-// the default is 1.
-#ifndef GEMM_CLUSTER
-#define GEMM_CLUSTER 1
-#endif
 
 enum { MODE_PAIR = 0, MODE_SYRK = 1, MODE_PLAIN = 2 };
 
@@ -238,9 +231,6 @@ struct GemmParams {
   const double* seg_sign;  // [nr]
   double* dpart;           // [nsplit][nv][nv]
   int* err;
-  // cluster of CL CTAs along N sharing the A tile (multicast)
-  int ntg;      // groups of CL adjacent N tiles
-  int njobs_c;  // cluster jobs
 };
 
 template <int BN>
@@ -276,52 +266,6 @@ __device__ __forceinline__ bool decode_job(const GemmParams& P, int job, int* sl
   return true;
 }
 
-// Own tile (mt, nt) of a cluster job: whether it is computed and written.
-template <int BN>
-__device__ __forceinline__ bool tile_valid(const GemmParams& P, int mt, int nt) {
-  if (nt >= P.ntn) return false;
-  if (P.mode == MODE_PAIR) {
-    const int r0 = mt * BM, c0 = nt * BN;
-    if (r0 + BM <= P.na && c0 + BN <= P.na) return false;
-    if (P.energy_only && (r0 + BM <= P.na || c0 + BN <= P.na)) return false;
-  } else if (P.mode == MODE_SYRK) {
-    if (nt < (mt * BM) / BN) return false;
-  }
-  return true;
-}
-
-// Cluster job -> (slot, mt, N group g); the CTA of rank r owns tile
-// nt = g CL + r.  Returns false when no rank of the group has a valid tile.
-template <int BN, int CL>
-__device__ __forceinline__ bool decode_group(const GemmParams& P, int job, int* slot, int* mt, int* g) {
-  if (P.mode == MODE_PAIR) {
-    const int per = P.ntm * P.ntg;
-    *slot = job / per;
-    const int rem = job % per;
-    *mt = rem / P.ntg;
-    *g = rem % P.ntg;
-  } else if (P.mode == MODE_PLAIN) {
-    *slot = 0;
-    *mt = job / P.ntg;
-    *g = job % P.ntg;
-  } else {
-    int per = 0;
-    for (int m = 0; m < P.ntm; ++m) per += P.ntg - ((m * BM) / BN) / CL;
-    *slot = job / per;
-    int rem = job % per, m = 0;
-    while (rem >= P.ntg - ((m * BM) / BN) / CL) {
-      rem -= P.ntg - ((m * BM) / BN) / CL;
-      ++m;
-    }
-    *mt = m;
-    *g = ((m * BM) / BN) / CL + rem;
-  }
-  bool any = false;
-#pragma unroll
-  for (int r = 0; r < CL; ++r) any = any || tile_valid<BN>(P, *mt, *g * CL + r);
-  return any;
-}
-
 __device__ __forceinline__ void seg_range(const GemmParams& P, int split, int* r0, int* r1) {
   if (P.mode != MODE_SYRK) {
     *r0 = 0;
@@ -350,17 +294,11 @@ struct Cfg {
   static_assert(2 * SET_COLS + 2 * (TAIL_COLS > 0 ? TAIL_COLS : 0) <= TMEM_COLS, "TMEM budget");
 };
 
-template <int KS, int BN, int STAGES, int CL>
+template <int KS, int BN, int STAGES>
 __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                              const __grid_constant__ CUtensorMap mapB,
                                                              GemmParams P) {
   using C = Cfg<KS, BN, STAGES>;
-  static_assert(CL == 1 || CL == 2 || CL == 4, "cluster size");
-  // cluster of CL CTAs along N: rank r loads rows [r BM/CL, (r+1) BM/CL) of
-  // the shared A tile (every plane) and multicasts them to the whole cluster
-  const int rank = CL > 1 ? (int)tc::cluster_ctarank() : 0;
-  const int cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-  constexpr uint16_t MASK = (uint16_t)((1u << CL) - 1u);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
@@ -377,7 +315,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full[s], 1);
-      tc::mbar_init(&empty[s], CL);  // released by the MMAs of every CTA of the cluster
+      tc::mbar_init(&empty[s], 1);
     }
     for (int q = 0; q < 2; ++q) {
       tc::mbar_init(&tfull[q], 1);
@@ -396,7 +334,6 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
   if (warp == 1) tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
   tc::tc_fence_before();
   __syncthreads();
-  if (CL > 1) tc::cluster_sync();  // peers' barriers initialised before any multicast reaches them
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -404,10 +341,9 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
     // ---------------------------------------------------------- TMA producer
     if (lane == 0) {
       uint32_t it = 0;
-      for (int job = cid; job < P.njobs_c && !*abort_flag; job += ncl) {
-        int slot, mt, g;
-        if (!decode_group<BN, CL>(P, job, &slot, &mt, &g)) continue;
-        const int nt = g * CL + rank;
+      for (int job = blockIdx.x; job < P.njobs && !*abort_flag; job += gridDim.x) {
+        int slot, mt, nt;
+        if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
         int r0, r1;
         seg_range(P, slot, &r0, &r1);
         for (int r = r0; r < r1; ++r) {
@@ -433,14 +369,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             }
             uint8_t* sa = smem + s * C::STAGE_BYTES;
             tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-            if (CL == 1) {
-              tc::tma_load_3d(sa, &mapA, kb * BKE, arow, 0, &full[s]);
-            } else {
-#pragma unroll
-              for (int p = 0; p < KS; ++p)
-                tc::tma_load_3d_mc(sa + p * C::A_SLICE + rank * (C::A_SLICE / CL), &mapA, kb * BKE,
-                                   arow + rank * (BM / CL), p, &full[s], MASK);
-            }
+            tc::tma_load_3d(sa, &mapA, kb * BKE, arow, 0, &full[s]);
             tc::tma_load_3d(sa + C::A_BYTES, &mapB, kb * BKE, brow, 0, &full[s]);
           }
           if (*abort_flag) break;
@@ -452,9 +381,9 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
     constexpr uint32_t IDESC = tc::make_idesc_bf16(BM, BN);
     uint32_t it = 0, chunk = 0, segc = 0;
     if (lane == 0) {
-      for (int job = cid; job < P.njobs_c && !*abort_flag; job += ncl) {
-        int slot, mt, g;
-        if (!decode_group<BN, CL>(P, job, &slot, &mt, &g)) continue;
+      for (int job = blockIdx.x; job < P.njobs && !*abort_flag; job += gridDim.x) {
+        int slot, mt, nt;
+        if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
         int r0, r1;
         seg_range(P, slot, &r0, &r1);
         for (int r = r0; r < r1 && !*abort_flag; ++r) {
@@ -513,8 +442,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
                 }
               }
             }
-            if (CL == 1) tc::mma_commit(&empty[s]);
-            else tc::mma_commit_mc(&empty[s], MASK);
+            tc::mma_commit(&empty[s]);
             if (kc == KCHUNK_BLOCKS - 1 || kb == P.nkb - 1) {
               tc::mma_commit(&tfull[set]);
               ++chunk;
@@ -535,11 +463,9 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     const int row = q * 32 + lane;
     uint32_t chunk = 0, segc = 0;
-    for (int job = cid; job < P.njobs_c; job += ncl) {
-      int slot, mt, g;
-      if (!decode_group<BN, CL>(P, job, &slot, &mt, &g)) continue;
-      const int nt = g * CL + rank;
-      const bool own = tile_valid<BN>(P, mt, nt);
+    for (int job = blockIdx.x; job < P.njobs; job += gridDim.x) {
+      int slot, mt, nt;
+      if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
       int r0, r1;
       seg_range(P, slot, &r0, &r1);
       float hi[BN], lo[BN];
@@ -614,7 +540,6 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
       }
       if (failed) break;
       // ------------------------------------------------------ tile output
-      if (!own) continue;  // a cluster neighbour's tile outside the output
       if (P.mode == MODE_PAIR) {
         const int2 pr = P.pairs[slot];
         const int a = mt * BM + row;
@@ -657,8 +582,6 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
   __syncwarp();
   tc::tc_fence_before();
   __syncthreads();
-  // no CTA leaves while a peer may still multicast into it or arrive on it
-  if (CL > 1) tc::cluster_sync();
   tc::tc_fence_after();
   if (warp == 1) tc::tmem_dealloc(tmem, C::TMEM_COLS);
 }
@@ -714,49 +637,18 @@ int num_sms() {
   return n > 0 ? n : 148;
 }
 
-template <int KS, int BN, int STAGES, int CL>
+template <int KS, int BN, int STAGES>
 int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kpad, GemmParams P,
                 cudaStream_t st) {
   using C = Cfg<KS, BN, STAGES>;
+  if (P.njobs <= 0) return DSRG_FNO_OK;
   CUtensorMap ma, mb;
-  DSRG_TRY(make_plane_map(&ma, pa, KS, rows_a, Kpad, BM / CL, CL == 1 ? KS : 1));
+  DSRG_TRY(make_plane_map(&ma, pa, KS, rows_a, Kpad, BM, KS));
   DSRG_TRY(make_plane_map(&mb, pb, KS, rows_b, Kpad, BN, KS));
-  auto kern = sliced_gemm_kernel<KS, BN, STAGES, CL>;
+  auto kern = sliced_gemm_kernel<KS, BN, STAGES>;
   // the same value on every launch (per device, idempotent, thread-safe)
   DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-  // cluster jobs: groups of CL adjacent N tiles
-  P.ntg = ceil_div(P.ntn, CL);
-  if (P.mode == MODE_PAIR) {
-    P.njobs_c = P.njobs / (P.ntm * P.ntn) * P.ntm * P.ntg;
-  } else if (P.mode == MODE_PLAIN) {
-    P.njobs_c = P.ntm * P.ntg;
-  } else {
-    int per = 0;
-    for (int m = 0; m < P.ntm; ++m) per += P.ntg - ((m * BM) / BN) / CL;
-    P.njobs_c = per * P.nsplit;
-  }
-  if (P.njobs_c <= 0) return DSRG_FNO_OK;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.blockDim = dim3(192);
-  cfg.dynamicSmemBytes = C::SMEM;
-  cfg.stream = st;
-  int nclusters = num_sms() / CL;
-  if (CL > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(CL * nclusters);
-    int maxc = 0;
-    DSRG_CUDA(cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg));
-    if (maxc < 1) return DSRG_FNO_ERR_UNSUPPORTED;
-    nclusters = std::min(nclusters, maxc);
-  }
-  nclusters = std::min(nclusters, P.njobs_c);
-  cfg.gridDim = dim3(CL * nclusters);
+  const int grid = std::min(num_sms(), P.njobs);
   void* tok = nullptr;
   if (profiling()) {
     // executed tensor-core flops of the output tiles: tiles x 2 BM BN Kpad x digit products
@@ -779,7 +671,7 @@ int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kp
                                                                                       : "sliced_gemm_plain");
     prof_begin(nm, fl, st, &tok);
   }
-  DSRG_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, P));
+  kern<<<grid, 192, C::SMEM, st>>>(ma, mb, P);
   DSRG_LAUNCH_CHECK();
   prof_end(tok, st);
   return DSRG_FNO_OK;
@@ -788,11 +680,11 @@ int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kp
 int dispatch_gemm(int KS, const void* pa, long rows_a, const void* pb, long rows_b, int Kpad, GemmParams P,
                   cudaStream_t st) {
   switch (KS) {
-    case 3: return launch_gemm<3, 64, 3, GEMM_CLUSTER>(pa, rows_a, pb, rows_b, Kpad, P, st);
-    case 4: return launch_gemm<4, 64, 2, GEMM_CLUSTER>(pa, rows_a, pb, rows_b, Kpad, P, st);
-    case 5: return launch_gemm<5, 48, 2, GEMM_CLUSTER>(pa, rows_a, pb, rows_b, Kpad, P, st);
+    case 3: return launch_gemm<3, 64, 3>(pa, rows_a, pb, rows_b, Kpad, P, st);
+    case 4: return launch_gemm<4, 64, 2>(pa, rows_a, pb, rows_b, Kpad, P, st);
+    case 5: return launch_gemm<5, 48, 2>(pa, rows_a, pb, rows_b, Kpad, P, st);
     // 6 planes (21 products): TMEM allows N = 32, shared memory one stage
-    case 6: return P.mode == MODE_PLAIN ? launch_gemm<6, 32, 1, 1>(pa, rows_a, pb, rows_b, Kpad, P, st)
+    case 6: return P.mode == MODE_PLAIN ? launch_gemm<6, 32, 1>(pa, rows_a, pb, rows_b, Kpad, P, st)
                                         : DSRG_FNO_ERR_ARG;
     default: return DSRG_FNO_ERR_ARG;
   }

@@ -59,3 +59,42 @@ def test_missing_library_fails_loudly(tmp_path):
             binding.load(str(tmp_path / "nope.so"))
     finally:
         binding._lib = saved
+
+
+def test_noalloc_rejects_oversize_and_host_pointers_before_any_work():
+    """dsrg_fno_truncate_noalloc checks its arguments on the host: nvir above
+    the fixed scratch limit, and host (not device) arrays, return
+    DSRG_FNO_ERR_ARG with a message to the log callback and no GPU work."""
+    import numpy as np
+
+    import paper_2312_07008_gb300 as pkg
+    lib = pkg.load()
+    msgs = []
+    pkg.dsrg_fno_set_log_callback(lambda level, text: msgs.append((level, text)))
+    try:
+        k = ctypes.c_int32(-7)
+        nv = 4
+        d = np.eye(nv)
+        on = np.zeros(nv)
+        no = np.zeros((nv, nv))
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        st = lib.dsrg_fno_truncate_noalloc(513, vp(d), 0, 98.5, 0.01, vp(on), vp(no), ctypes.byref(k), None)
+        assert st == -1
+        assert any("512" in t for _, t in msgs), msgs
+        st = lib.dsrg_fno_truncate_noalloc(nv, vp(d), 0, 98.5, 0.01, vp(on), vp(no), ctypes.byref(k), None)
+        assert st == -1
+        assert any("device memory" in t for _, t in msgs), msgs
+        assert k.value == -7 and not on.any()
+    finally:
+        pkg.dsrg_fno_set_log_callback(None)
+
+
+def test_log_callback_can_be_cleared():
+    import paper_2312_07008_gb300 as pkg
+    lib = pkg.load()
+    msgs = []
+    pkg.dsrg_fno_set_log_callback(lambda level, text: msgs.append(text))
+    pkg.dsrg_fno_set_log_callback(None)
+    k = ctypes.c_int32()
+    assert lib.dsrg_fno_truncate_noalloc(600, None, 0, 98.5, 0.01, None, None, ctypes.byref(k), None) == -1
+    assert msgs == []
