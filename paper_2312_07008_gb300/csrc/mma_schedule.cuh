@@ -54,4 +54,14 @@ __host__ __device__ constexpr StackedMma stacked_mma(int ks, int i, int nexact =
   return StackedMma{-1, 0, 0, 0};
 }
 
+// Every MMA of the schedule has a valid N for M = 128 (a multiple of 16,
+// 16 .. 256) when the level width is bn.
+__host__ __device__ constexpr bool stacked_n_valid(int ks, int bn, int nexact = kExactLevels) {
+  for (int i = 0; i < stacked_mma_count(ks, nexact); ++i) {
+    const int n = stacked_mma(ks, i, nexact).nb * bn;
+    if (n % 16 != 0 || n < 16 || n > 256) return false;
+  }
+  return true;
+}
+
 }  // namespace dsrg

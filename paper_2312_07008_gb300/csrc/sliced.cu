@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "mma_schedule.cuh"
 #include "tc_ptx.cuh"
 
 namespace dsrg {
@@ -42,7 +43,7 @@ constexpr int BM = 128;
 constexpr int BKE = 64;            // k elements per block (128 bytes of bf16, 128-byte swizzle)
 constexpr int ROW_BYTES = 2 * BKE;
 constexpr int KCHUNK_BLOCKS = 320 / BKE;  // 320 k-values per exact sum of levels 0, 1, 2
-constexpr int NEXACT = 3;          // levels kept exact per chunk
+constexpr int NEXACT = kExactLevels;  // levels kept exact per chunk (3)
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
 
 enum { MODE_PAIR = 0, MODE_SYRK = 1, MODE_PLAIN = 2 };
@@ -292,6 +293,7 @@ struct Cfg {
   static constexpr int TAIL_BASE = 2 * SET_COLS;             // lower levels of one segment
   static constexpr int TAIL_COLS = (KS - NEXACT) * BN;
   static_assert(2 * SET_COLS + 2 * (TAIL_COLS > 0 ? TAIL_COLS : 0) <= TMEM_COLS, "TMEM budget");
+  static_assert(stacked_n_valid(KS, BN, NEXACT), "stacked MMA widths");
 };
 
 template <int KS, int BN, int STAGES>
@@ -378,7 +380,6 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    constexpr uint32_t IDESC = tc::make_idesc_bf16(BM, BN);
     uint32_t it = 0, chunk = 0, segc = 0;
     if (lane == 0) {
       for (int job = blockIdx.x; job < P.njobs && !*abort_flag; job += gridDim.x) {
@@ -421,25 +422,30 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             const uint32_t b_base = a_base + C::A_BYTES;
             const uint64_t a_desc0 = tc::make_sdesc_sw128(a_base);
             const uint64_t b_desc0 = tc::make_sdesc_sw128(b_base);
+            // Stacked-B schedule: the products of A plane m.a with the
+            // consecutive B planes m.b0 .. m.b0 + m.nb - 1 belong to the
+            // consecutive levels m.level .. m.level + m.nb - 1, which lie one
+            // after another in TMEM, and the B planes lie one after another in
+            // shared memory: one MMA with N = m.nb BN does them all.
 #pragma unroll
-            for (int sa = 0; sa < KS; ++sa) {
+            for (int i = 0; i < stacked_mma_count(KS, NEXACT); ++i) {
+              const StackedMma m = stacked_mma(KS, i, NEXACT);
+              // exact levels: per chunk (restart at the chunk's first block);
+              // lower levels: per segment (restart at the segment's first block)
+              const bool exact = m.level < NEXACT;
+              const uint32_t d = exact ? tmem + set * C::SET_COLS + m.level * BN
+                                       : tmem + C::TAIL_BASE + lt * C::TAIL_COLS + (m.level - NEXACT) * BN;
+              const bool first_block = exact ? (kc == 0) : (kb == 0);
+              const uint32_t idesc = tc::make_idesc_bf16(BM, m.nb * BN);
 #pragma unroll
-              for (int sb = 0; sb < KS - sa; ++sb) {
-                const int L = sa + sb;
-                // exact levels: per chunk (restart at the chunk's first block);
-                // lower levels: per segment (restart at the segment's first block)
-                const bool exact = L < NEXACT;
-                const uint32_t d = exact ? tmem + set * C::SET_COLS + L * BN
-                                         : tmem + C::TAIL_BASE + lt * C::TAIL_COLS + (L - NEXACT) * BN;
-                const bool first_block = exact ? (kc == 0) : (kb == 0);
-#pragma unroll
-                for (int kk = 0; kk < BKE / 16; ++kk) {
-                  // start-address field += byte offset / 16 (no carry: shared addresses < 2^18)
-                  const uint64_t ad = a_desc0 + (uint64_t)((sa * C::A_SLICE + kk * 32) >> 4);
-                  const uint64_t bd = b_desc0 + (uint64_t)((sb * C::B_SLICE + kk * 32) >> 4);
-                  const uint32_t acc = (first_block && kk == 0 && sa == 0) ? 0u : 1u;
-                  tc::mma_bf16(d, ad, bd, IDESC, acc);
-                }
+              for (int kk = 0; kk < BKE / 16; ++kk) {
+                // start-address field += byte offset / 16 (no carry: shared addresses < 2^18)
+                const uint64_t ad = a_desc0 + (uint64_t)((m.a * C::A_SLICE + kk * 32) >> 4);
+                const uint64_t bd = b_desc0 + (uint64_t)((m.b0 * C::B_SLICE + kk * 32) >> 4);
+                // the MMA of A plane 0 covers every level of its set and comes
+                // first: it alone starts a fresh accumulation
+                const uint32_t acc = (first_block && kk == 0 && m.a == 0) ? 0u : 1u;
+                tc::mma_bf16(d, ad, bd, idesc, acc);
               }
             }
             tc::mma_commit(&empty[s]);
