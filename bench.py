@@ -49,7 +49,6 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--nslices", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the float64 GPU form (0: skip)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="length of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -139,51 +138,217 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle
-def cpu_baseline(p, seconds):
-    """The oracle as it stands on the host cores: its vv-class energy and D_vv
-    term 4 for core-core pairs, one pair at a time until `seconds` pass; the
-    rate is scaled to a whole solve by the algorithmic flops covered."""
-    import numpy as np  # noqa: F401
-    import oracle as O
-    nc = p.ncore
-    pairs = [(m, n) for m in range(nc) for n in range(m, nc)]
-    t0 = time.perf_counter()
-    done = 0
-    covered = 0.0
-    for (m, n) in pairs:
-        O.e_vv(p, components=[[(m, n)] if m == n else [(m, n), (n, m)]])
-        O.dvv_terms(p, terms=(4,), core_pairs=[(m, n)])
-        done += 1
-        covered += 2.0 * p.naux * p.nvir ** 2 + (1 if m == n else 2) * float(p.nvir) ** 3
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
-    frac = covered / algorithmic_flops(p)
+class OracleSample:
+    """Stratified timing of one oracle solve (oracle.solve: E_vv, D_vv terms
+    1-12, NOs, and per cut the FNO problem and its E_vv) on the host cores.
+
+    The solve's work falls into strata whose unit costs differ; each stratum
+    is timed on a sample of its units through the oracle's own functions, and
+    the solve's time is the sum of unit time x unit count:
+      amp     semi-internal amplitudes for a subset of the holes (cost ~ holes^2) and T1
+      small   Eq. A12 terms 1-3, 6, 8-12 (whole)
+      cc      core pairs m < n: E_vv group {mn, nm} and term 4; m = n likewise
+      ca      core m: E_vv group {mu, um}_u; term 5 = its amplitude blocks
+              + one unit per active u (two calls separate the two)
+      aa      active pairs: E_vv group; term 7 = its amplitude blocks + one
+              unit per (u, v) (two calls)
+      no      NOs of a symmetric nvir x nvir matrix
+      corr    per cut: recanonicalisation, the rotated problem, and E_vv of
+              a sample of its groups (by kind, scaled by counts)
+    The semi-internal amplitudes and T1 of the whole problem, built once per
+    process outside the timed samples, feed the term samples.  Groups of
+    strata are timed one at a time (`run_group`), so a step can stay short."""
+
+    def __init__(self, p, nkept):
+        import oracle as O
+        self.O, self.p = O, p
+        self.nkept = [int(k) for k in nkept]
+        nc, na = p.ncore, p.nact
+        self.ts = O.t2_semi_internal(p) if na else None
+        self.t1 = O.t1_amplitudes(p, self.ts)
+        self.unit = {}      # stratum -> measured seconds per unit (latest)
+        self.count = {}     # stratum -> units per solve
+        groups = [["amp", "small", "no"], ["cc"]]
+        if na:
+            groups += [["ca_evv"], ["ca_t5a"], ["ca_t5b"], ["aa_evv"], ["aa_t7a"], ["aa_t7b"]]
+        groups += [[f"corr{i}"] for i in range(len(self.nkept))]
+        self.groups = groups
+        self.next = 0
+
+    def _t(self, f):
+        t0 = time.perf_counter()
+        f()
+        return time.perf_counter() - t0
+
+    def _stratum(self, name):
+        O, p = self.O, self.p
+        nc, na, nh = p.ncore, p.nact, p.ncore + p.nact
+        ts, t1 = self.ts, self.t1
+        if name == "amp":
+            k = max(1, min(nh, int(round(nh / 5))))
+            h = list(range(0, nh, max(1, nh // k)))[:k]
+            dt = self._t(lambda: O.t2_semi_internal(p, holes=h)) if na else 0.0
+            dt += self._t(lambda: O.t1_amplitudes(p, ts))
+            self.unit["amp"], self.count["amp"] = dt, 1.0
+            if na:   # the amplitude build scales with the ordered hole pairs
+                self.unit["amp"] = dt * (nh / len(h)) ** 2
+            return dt
+        if name == "small":
+            dt = self._t(lambda: O.dvv_terms(p, terms=(1, 2, 3, 6, 8, 9, 10, 11, 12), ts=ts, t1=t1))
+            self.unit["small"], self.count["small"] = dt, 1.0
+            return dt
+        if name == "no":
+            rng = __import__("numpy").random.default_rng(0)
+            a = rng.standard_normal((p.nvir, p.nvir))
+            d = a + a.T
+            dt = self._t(lambda: O.natural_orbitals(d))
+            self.unit["no"], self.count["no"] = dt, 1.0
+            return dt
+        if name == "cc":
+            dt = 0.0
+            off = [(m, (m + 1 + 7 * m) % nc) for m in range(0, nc, max(1, nc // 3))][:3] if nc > 1 else []
+            off = [(min(a, b), max(a, b)) for a, b in off if a != b]
+            for (m, n) in off:
+                dt_p = self._t(lambda: O.e_vv(p, components=[[(m, n), (n, m)]]))
+                dt_p += self._t(lambda: O.dvv_terms(p, terms=(4,), ts=ts, t1=t1, core_pairs=[(m, n)]))
+                dt += dt_p
+            if off:
+                self.unit["cc_off"] = dt / len(off)
+                self.count["cc_off"] = nc * (nc - 1) / 2
+            m = nc // 2
+            dd = self._t(lambda: O.e_vv(p, components=[[(m, m)]]))
+            dd += self._t(lambda: O.dvv_terms(p, terms=(4,), ts=ts, t1=t1, core_pairs=[(m, m)]))
+            self.unit["cc_diag"], self.count["cc_diag"] = dd, float(nc)
+            return dt + dd
+        m = nc // 2
+        if name == "ca_evv":
+            comp = [(m, nc + u) for u in range(na)] + [(nc + u, m) for u in range(na)]
+            dt = self._t(lambda: O.e_vv(p, components=[comp]))
+            self.unit["ca_evv"], self.count["ca_evv"] = dt, float(nc)
+            return dt
+        if name in ("ca_t5a", "ca_t5b"):
+            sel = [(m, 0)] if name == "ca_t5a" else [(m, 1 % na), (m, 2 % na)]
+            sel = list(dict.fromkeys(sel))
+            dt = self._t(lambda: O.dvv_terms(p, terms=(5,), ts=ts, t1=t1, ca_pairs=sel))
+            self.unit[name] = (dt, len(sel))
+            self._split("ca_t5", nc, na)
+            return dt
+        if name == "aa_evv":
+            comp = [(nc + u, nc + v) for u in range(na) for v in range(na)]
+            dt = self._t(lambda: O.e_vv(p, components=[comp]))
+            self.unit["aa_evv"], self.count["aa_evv"] = dt, 1.0
+            return dt
+        if name in ("aa_t7a", "aa_t7b"):
+            sel = [(0, 0)] if name == "aa_t7a" else [(0, 1 % na), (1 % na, 0)]
+            sel = list(dict.fromkeys(sel))
+            dt = self._t(lambda: O.dvv_terms(p, terms=(7,), ts=ts, t1=t1, aa_pairs=sel))
+            self.unit[name] = (dt, len(sel))
+            self._split("aa_t7", 1, na * na)
+            return dt
+        if name.startswith("corr"):
+            return self._corr(int(name[4:]))
+        raise KeyError(name)
+
+    def _split(self, key, groups, units):
+        """Two timings with 1 and 2 units: fixed part per group + per-unit part."""
+        a, b = self.unit.get(key + "a"), self.unit.get(key + "b")
+        if not a or not b:
+            return
+        (ta, na_), (tb, nb) = a, b
+        per = max(0.0, (tb - ta) / max(nb - na_, 1)) if nb != na_ else ta / na_
+        fixed = max(0.0, ta - na_ * per)
+        self.unit[key] = fixed + units * per
+        self.count[key] = float(groups)
+
+    def _corr(self, i):
+        O, p = self.O, self.p
+        import numpy as np
+        k = self.nkept[i]
+        rng = np.random.default_rng(1 + i)
+        q, _ = np.linalg.qr(rng.standard_normal((p.nvir, p.nvir)))
+        t0 = time.perf_counter()
+        U, eps_new = O.recanonicalize(p, q, k)
+        pf = O.fno_problem(p, U, eps_new)
+        comps = O.hole_pair_components(pf)
+        fixed = time.perf_counter() - t0
+        kinds = {}
+        for c in comps:
+            kinds.setdefault(len(c), []).append(c)
+        dt = fixed
+        est = fixed
+        for size, cs in kinds.items():
+            take = cs[:: max(1, len(cs) // 3)][:3]
+            t = self._t(lambda: O.e_vv(pf, components=take))
+            dt += t
+            est += t / len(take) * len(cs)
+        self.unit[f"corr{i}"], self.count[f"corr{i}"] = est, 1.0
+        return dt
+
+    def run_group(self):
+        """Times the next group of strata; returns the seconds measured."""
+        g = self.groups[self.next % len(self.groups)]
+        self.next += 1
+        return sum(self._stratum(nm) for nm in g)
+
+    def complete(self):
+        return self.next >= len(self.groups)
+
+    def solve_seconds(self):
+        return sum(v * self.count[k] for k, v in self.unit.items() if k in self.count and not isinstance(v, tuple))
+
+
+def _oracle_cores():
     cores = os.cpu_count()
     try:
         from threadpoolctl import threadpool_info
         cores = max(i.get("num_threads", 1) for i in threadpool_info()) or cores
     except Exception:
         pass
-    return {"value": frac / dt, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} core-core pair(s) of E_vv + D_vv term 4 in {dt:.1f} s, "
-                      f"{frac:.3e} of a solve's algorithmic flops, scaled"}
+    return cores
 
 
-def batch_cpu_baseline(seconds):
-    """The oracle on the largest instance of the ragged batch, as in
-    cpu_baseline, rescaled from that instance's flops to the batch's
+def cpu_baseline(p, nkept):
+    """The oracle as it stands on the host cores: one stratified sample of a
+    whole solve (OracleSample, every group once), extrapolated to solves/s."""
+    s = OracleSample(p, nkept)
+    measured = 0.0
+    while not s.complete():
+        measured += s.run_group()
+    sec = s.solve_seconds()
+    return {"value": 1.0 / sec, "unit": "solves/s", "cores": _oracle_cores(), "kind": "oracle",
+            "sample": f"stratified sample of one oracle solve ({len(s.groups)} groups of strata: amplitudes, "
+                      f"small terms, core pairs, core-active groups, active pairs, NOs, {len(nkept)} FNO "
+                      f"corrections), {measured:.1f} s timed, extrapolated by unit counts to {sec:.0f} s "
+                      f"per solve"}
+
+
+def batch_cpu_baseline(nkept_by_instance):
+    """The oracle's stratified sample on the largest instance of the ragged
+    batch, rescaled from that instance's flops to the batch's mean
     (instances per second of the whole 64-instance mix)."""
     from synth.problems import batch_sizes, batch_problem
     sizes = batch_sizes()
     fl = [algorithmic_flops(types.SimpleNamespace(**s)) for s in sizes]
     k = max(range(len(sizes)), key=lambda i: fl[i])
-    r = cpu_baseline(batch_problem(k), seconds)
+    r = cpu_baseline(batch_problem(k), [nkept_by_instance[k]])
     flops_per_s = r["value"] * fl[k]
     r["value"] = flops_per_s / (sum(fl) / len(fl))
     r["unit"] = "instances/s"
     r["sample"] = f"instance {k} of the batch (largest): " + r["sample"] + "; rescaled by the batch's mean flops"
     return r
+
+
+def reference_nkept(name, p):
+    """N' per cut for the correction strata of the reference arm: the stored
+    oracle values of the workload when present, else 15 % of nvir."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    cuts = cuts_of(name)
+    try:
+        with open(path) as f:
+            g = json.load(f)
+        return [int(g["cuts"][str(c)]["nkept"]) for c in cuts]
+    except (OSError, KeyError, ValueError):
+        return [max(1, int(0.15 * p.nvir)) for _ in cuts]
 
 
 def single_config(p, name, cuts, nslices):
@@ -205,31 +370,49 @@ def batch_config(nslices):
 
 
 def reference_arm(args):
+    """The oracle timed on the host cores.  A step times one group of strata
+    of OracleSample (a bounded sample of the workload's solve); groups rotate
+    over the warm-up and timed steps, and the value is the solves/s of the
+    whole solve extrapolated from the latest timing of every stratum.
+    ms_per_step is the measured length of a timed step."""
     from synth import workload
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     batch = args.workload == BATCH_WORKLOAD
     if batch:
-        base = lambda sec: batch_cpu_baseline(sec)  # noqa: E731
+        from synth.problems import batch_sizes, batch_problem
+        sizes = batch_sizes()
+        fl = [algorithmic_flops(types.SimpleNamespace(**sz)) for sz in sizes]
+        k = max(range(len(sizes)), key=lambda i: fl[i])
+        p = batch_problem(k)
+        nk = [max(1, int(0.15 * p.nvir))]
         config = batch_config(args.nslices)
+        scale = fl[k] / (sum(fl) / len(fl))
+        unit = "instances/s"
     else:
         p = workload(args.workload)
-        base = lambda sec: cpu_baseline(p, sec)  # noqa: E731
+        nk = reference_nkept(args.workload, p)
         config = single_config(p, args.workload, cuts_of(args.workload), args.nslices)
-    vals = []
+        scale = 1.0
+        unit = "solves/s"
+    s = OracleSample(p, nk)
     for _ in range(args.warmup):
-        base(max(2.0, args.cpu_seconds / 4))
-    for _ in range(args.steps):
-        vals.append(base(args.cpu_seconds))
-    v = sum(x["value"] for x in vals) / len(vals)
-    unit = vals[0]["unit"]
+        s.run_group()
+    times = [s.run_group() for _ in range(args.steps)]
+    while not s.complete():
+        s.run_group()
+    v = scale / s.solve_seconds()
+    sample = (f"one group of strata of a stratified oracle solve per step ({len(s.groups)} groups rotate), "
+              f"extrapolated by unit counts to {s.solve_seconds():.0f} s per solve"
+              + ("; largest batch instance, rescaled by the batch's mean flops" if batch else ""))
+    ms = 1e3 * sum(times) / max(len(times), 1)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config,
-            "cpu_baseline": {"value": v, "unit": unit, "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": _oracle_cores(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -383,7 +566,7 @@ def main():
         "result": {"e2": res["e2"], **{f"nkept_{c}": res[c][0] for c in cuts}, **{f"de_{c}": res[c][1] for c in cuts}},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(p, [res[c][0] for c in cuts])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -588,7 +771,7 @@ def batch_arm(args):
                    "sum_de": sum(r["de"] for r in res)},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = batch_cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = batch_cpu_baseline([r["nkept"] for r in res])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -265,9 +265,13 @@ def e_vv(prob, components=None):
 # --------------------------------------------------------------------------
 # D_vv (Eq. A12, terms 1-12; the Lambda3 term 13 only with a 3-cumulant)
 # --------------------------------------------------------------------------
-def dvv_terms(prob, terms=range(1, 14), ts=None, t1=None, core_pairs=None, lambda3=None):
+def dvv_terms(prob, terms=range(1, 14), ts=None, t1=None, core_pairs=None, lambda3=None, ca_pairs=None,
+              aa_pairs=None):
     """Returns {term number: [nvir][nvir] contribution} for Eq. A12.
-    `core_pairs` restricts term 4 to the listed unordered core pairs (m <= n).
+    `core_pairs` restricts term 4 to the listed unordered core pairs (m <= n),
+    `ca_pairs` term 5 to the listed (m, u) (the sum over v kept whole), and
+    `aa_pairs` term 7 to the listed (u, v) (the sum over x, y kept whole):
+    partial sums, used to time a sample of the oracle.
     Term 13 is formed only when `lambda3` ([na]^6, Lambda^{xyz}_{uvw}) is given."""
     sp = spaces(prob)
     nc, na, nv = sp.nc, sp.na, sp.nv
@@ -307,9 +311,12 @@ def dvv_terms(prob, terms=range(1, 14), ts=None, t1=None, core_pairs=None, lambd
         out[4] = d
     if na and 5 in want:   # S(t^{mu}_{ee'} tcheck^{mv}_{fe'}) Gamma^u_v
         d = np.zeros((nv, nv))
-        for m in range(nc):
+        msel = range(nc) if ca_pairs is None else sorted({m for m, _ in ca_pairs})
+        for m in msel:
             Tm = [t2_vv(prob, m, nc + u)[0] for u in range(na)]   # t^{mu}; t^{um} = (t^{mu})^T
             for u in range(na):
+                if ca_pairs is not None and (m, u) not in ca_pairs:
+                    continue
                 for v in range(na):
                     g = G[u, v]
                     if g == 0.0:
@@ -332,6 +339,8 @@ def dvv_terms(prob, terms=range(1, 14), ts=None, t1=None, core_pairs=None, lambd
         d = np.zeros((nv, nv))
         for u in range(na):
             for v in range(na):
+                if aa_pairs is not None and (u, v) not in aa_pairs:
+                    continue
                 W = np.zeros((nv, nv))
                 for x in range(na):
                     for y in range(na):

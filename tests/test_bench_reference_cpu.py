@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def run_reference(*extra):
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2", "--warmup", "1",
-           "--cpu-seconds", "0.5", *extra]
+           *extra]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
@@ -36,6 +36,6 @@ def test_reference_line_single_workload():
 def test_reference_arm_other_ranks_print_nothing():
     env = dict(os.environ, RANK="1")
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0",
-           "--cpu-seconds", "0.2", "--workload", "sr_nocc10_nvir90_naux300"]
+           "--workload", "sr_nocc10_nvir90_naux300"]
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert out.returncode == 0 and not [l for l in out.stdout.splitlines() if l.startswith("{")]
