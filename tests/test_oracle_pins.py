@@ -549,3 +549,21 @@ def test_sa_lambda3_symmetries_and_partial_trace():
         spec = "".join(up[i] for i in perm) + "".join(lo[i] for i in perm)
         assert np.max(np.abs(np.einsum(f"{spec}->xyzuvw", lam3) - lam3)) <= 1e-13
     assert np.max(np.abs(np.einsum("xyzuvw->uvwxyz", lam3) - lam3)) <= 1e-13
+
+
+def test_sampling_restrictions_partition_terms_4_5_7():
+    """The restrictions of terms 4, 5 and 7 to listed core pairs, (m, u) and
+    (u, v) are partial sums: over a partition of the index set they add up to
+    the whole term, and the empty list gives zero."""
+    p = make_problem(ncore=3, nact=3, nvir=11, naux=23, seed=71, nstates=2)
+    nc, na = p.ncore, p.nact
+    full = O.dvv_terms(p, terms=(4, 5, 7))
+    cp = [(m, n) for m in range(nc) for n in range(m, nc)]
+    ca = [(m, u) for m in range(nc) for u in range(na)]
+    aa = [(u, v) for u in range(na) for v in range(na)]
+    for term, key, idx in ((4, "core_pairs", cp), (5, "ca_pairs", ca), (7, "aa_pairs", aa)):
+        halves = [idx[0::2], idx[1::2]]
+        parts = [O.dvv_terms(p, terms=(term,), **{key: h})[term] for h in halves]
+        ref = full[term]
+        assert np.max(np.abs(parts[0] + parts[1] - ref)) <= 1e-13 * np.max(np.abs(ref))
+        assert np.max(np.abs(O.dvv_terms(p, terms=(term,), **{key: []})[term])) == 0.0
