@@ -74,6 +74,36 @@ def algorithmic_flops(p):
     return float(p.naux) * p.nvir ** 2 * nh * (nh + 1) + float(nh) ** 2 * p.nvir ** 3
 
 
+def pair_alg_flops(p, nkept):
+    """Algorithmic flops of the pair contractions of one solve (the count of
+    the measurement plan): 2 naux nv^2 per unordered hole pair (i <= j), for
+    the D_vv pass (nv = nvir) and for the energy pass of every FNO cut
+    (nv = N')."""
+    nh = p.ncore + p.nact
+    pairs = nh * (nh + 1) / 2
+    return sum(2.0 * p.naux * float(v) ** 2 * pairs for v in [p.nvir] + list(nkept))
+
+
+def cut_margins(ons, p_o, nkept, degen_ratio=0.01):
+    """How far the p_o cut was from moving: with c(k) the cumulative ON
+    fraction of the k largest ONs and k0 the smallest k with c(k) >= p_o/100,
+    above = c(k0) - p_o/100 and below = p_o/100 - c(k0 - 1); the widening then
+    adds ONs while the relative gap to the next one is below degen_ratio, and
+    stop_gap is that relative gap where it stopped (N' = nkept)."""
+    import numpy as np
+    n = np.asarray(ons, dtype=np.float64)
+    c = np.cumsum(n) / np.sum(n)
+    t = p_o / 100.0
+    k0 = int(np.nonzero(c >= t)[0][0]) + 1 if np.any(c >= t) else len(n)
+    out = {"p_o": p_o, "nkept": int(nkept), "k0": k0, "above": float(c[k0 - 1] - t),
+           "below": float(t - (c[k0 - 2] if k0 >= 2 else 0.0)), "widened_by": int(nkept - k0)}
+    if 0 < nkept < len(n):
+        a, b = n[nkept - 1], n[nkept]
+        out["stop_gap"] = float((a - b) / max(a, b))
+        out["degen_ratio"] = degen_ratio
+    return out
+
+
 def cuts_of(name):
     from synth import CUTS
     return CUTS.get(name, (98.5,))
@@ -493,6 +523,7 @@ def main():
     for nm in COUNTERS:
         _, n_c, total = pkg.dsrg_fno_profile_query(nm)
         phases[nm] = {"calls": n_c, "mean": total / max(n_c, 1)}
+    ons_last = on.cpu().numpy()
     pair_ms, pair_n, pair_fl = pkg.dsrg_fno_profile_query("sliced_gemm_pair")
     syrk_ms, syrk_n, syrk_fl = pkg.dsrg_fno_profile_query("sliced_gemm_syrk")
     plain_ms, plain_n, plain_fl = pkg.dsrg_fno_profile_query("sliced_gemm_plain")
@@ -535,20 +566,34 @@ def main():
         gp64 = pkg.problem_from_synth(p, dev, pkg.FP64)
         step(gp64)
         barrier()
+        pkg.dsrg_fno_profile_enable(True)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.fp64_steps):
             r64 = step(gp64)
         f1.record(stream)
         barrier()
+        pkg.dsrg_fno_profile_enable(False)
         fms = f0.elapsed_time(f1) / args.fp64_steps
+        f64_ms, f64_n, _ = pkg.dsrg_fno_profile_query("pair_gemm_f64")
+        f64_alg = pair_alg_flops(p, [r64[c][0] for c in cuts]) * args.fp64_steps
+        f64_tf = f64_alg / (f64_ms / 1e3) / 1e12 if f64_ms > 0 else None
         fp64 = {"solves_per_s": 1e3 / fms, "s_per_solve": fms / 1e3, "gflops": flops / (fms / 1e3) / 1e9,
+                "roofline": {"bound": "fp64", "kernel": "pair_gemm_f64_kernel (float64 CUDA cores)",
+                             "achieved": f64_tf, "unit": "TFLOP/s", "launches": f64_n,
+                             "ms_per_step": f64_ms / args.fp64_steps,
+                             "peak": PEAKS_OWN["fp64_dgemm_tflops"],
+                             "peak_kind": "cuBLAS float64 GEMM (torch.matmul), measured by this repository",
+                             "frac": (f64_tf / PEAKS_OWN["fp64_dgemm_tflops"]) if f64_tf else None,
+                             "frac_of_nominal": (f64_tf / 1.25) if f64_tf else None,
+                             "nominal_tflops": 1.25},
                 "fast_minus_fp64": {"e2": res["e2"] - r64["e2"],
                                     **{f"de_{c}": res[c][1] - r64[c][1] for c in cuts},
                                     **{f"nkept_{c}": [res[c][0], r64[c][0]] for c in cuts}}}
 
+    alg = pair_alg_flops(p, [res[c][0] for c in cuts]) * args.steps
     roofline = roofline_of(pair_ms, pair_n, pair_fl, (syrk_ms, syrk_n, syrk_fl), (plain_ms, plain_n, plain_fl), ms,
-                           args.workload)
+                           args.workload, alg_flops=alg, nslices=args.nslices)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -563,7 +608,8 @@ def main():
         "phases": phases,
         "clocks": clocks,
         "fp64_form": fp64,
-        "result": {"e2": res["e2"], **{f"nkept_{c}": res[c][0] for c in cuts}, **{f"de_{c}": res[c][1] for c in cuts}},
+        "result": {"e2": res["e2"], **{f"nkept_{c}": res[c][0] for c in cuts}, **{f"de_{c}": res[c][1] for c in cuts},
+                   "cut_margins": [cut_margins(ons_last, c, res[c][0]) for c in cuts]},
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, [res[c][0] for c in cuts])
@@ -604,17 +650,33 @@ def traffic_per_launch(workload, exec_flops_per_launch):
     return t["bytes_per_exec_flop"] * exec_flops_per_launch
 
 
-def roofline_of(pair_ms, pair_n, pair_fl, syrk, plain, step_ms, workload=None):
+# Peaks this repository measured itself (the driver measures bf16 and HBM
+# only): cuBLAS float64 and TF32 GEMMs through torch.matmul, n = 8192, best
+# of several, CUDA events; the command and the clocks are in
+# profiles/peaks_fp64_tf32_gb300.md.
+PEAKS_OWN = {"fp64_dgemm_tflops": None, "tf32_tflops": None}
+
+
+def roofline_of(pair_ms, pair_n, pair_fl, syrk, plain, step_ms, workload=None, alg_flops=None, nslices=5):
+    """Roofline of the pair contraction (the dominant kernel).  `frac` counts
+    the algorithmic pair flops times the k(k+1)/2 digit products of k planes
+    (no tile padding); `frac_executed` the flops the tensor cores executed
+    (every 128 x N tile in full, K padded to 64)."""
     peaks, peak_kind = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    achieved = (pair_fl / (pair_ms / 1e3) / 1e12) if pair_ms > 0 else None
+    achieved_exec = (pair_fl / (pair_ms / 1e3) / 1e12) if pair_ms > 0 else None
+    prods = nslices * (nslices + 1) / 2
+    achieved = (alg_flops * prods / (pair_ms / 1e3) / 1e12) if (pair_ms > 0 and alg_flops) else None
     tf = lambda q: (q[2] / (q[0] / 1e3) / 1e12) if q[0] > 0 else None  # noqa: E731
     return {"bound": "tensor", "kernel": "sliced_gemm_kernel (pair contraction, tcgen05 bf16 digit planes)",
             "achieved": achieved, "peak": peak, "peak_kind": f"bf16 dense sustained, {peak_kind}",
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+            "count": f"algorithmic pair flops (2 naux nv^2 per hole pair i <= j) x {prods:.0f} digit products",
+            "achieved_executed": achieved_exec, "frac_executed": (achieved_exec / peak) if achieved_exec else None,
+            "padding": (pair_fl / (alg_flops * prods)) if alg_flops else None,
             "traffic": traffic_per_launch(workload, pair_fl / max(pair_n, 1)) if pair_n else None,
-            "traffic_note": "DRAM bytes per average pair launch: bytes per executed flop from one ncu capture of "
-                            "a full-size pair launch, times this run's executed flops per launch",
+            "traffic_note": "DRAM bytes per average pair launch: bytes per executed flop of one ncu capture of "
+                            "a small pair launch (profiles/), times this run's executed flops per launch",
             "launches": pair_n, "avg_launch_ms": pair_ms / max(pair_n, 1),
             "executed_flops_per_launch": pair_fl / max(pair_n, 1),
             "share_of_step": pair_ms / step_ms if step_ms > 0 else None,
@@ -750,7 +812,9 @@ def batch_arm(args):
                                     "max_abs_de": max(abs(a["de"] - b["de"]) for a, b in zip(rf, r64)),
                                     "nkept_equal": all(a["nkept"] == b["nkept"] for a, b in zip(rf, r64))}}
 
-    roofline = roofline_of(*q["sliced_gemm_pair"], q["sliced_gemm_syrk"], q["sliced_gemm_plain"], ms)
+    alg = sum(pair_alg_flops(pp, [r["nkept"]]) for pp, r in zip(probs, res)) * args.steps
+    roofline = roofline_of(*q["sliced_gemm_pair"], q["sliced_gemm_syrk"], q["sliced_gemm_plain"], ms,
+                           alg_flops=alg, nslices=args.nslices)
     roofline["note"] = "kernel times from a second, profiled run of the same steps"
     line = {
         "metric": METRIC, "value": value, "unit": "instances/s", "n_gpus": world, "steps": args.steps,

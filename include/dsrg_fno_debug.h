@@ -43,6 +43,23 @@ int dsrg_fno_debug_regularizer(int32_t n, const double* delta, double s, double*
  * nslices, a null pointer or max_entries below that number. */
 int dsrg_fno_debug_mma_schedule(int32_t nslices, int32_t* entries, int32_t max_entries);
 
+/* Output tiles of the pair contraction for one batch of hole pairs, host
+ * only: pairs[2k], pairs[2k+1] = (i, j), i <= j < ncore + nact; the tiles are
+ * 128-row x N-column blocks (N = 48 for 5 planes, 64 for 3 or 4) of the
+ * (nh np) x (nh np) matrix of all hole-particle rows; energy_only restricts
+ * the needed elements to virtual x virtual.  tiles[2t], tiles[2t+1] = (row
+ * tile, column tile) in the kernel's order.  Returns the tile count, or
+ * DSRG_FNO_ERR_ARG for bad arguments or max_tiles too small. */
+int dsrg_fno_debug_pair_tiles(int32_t nslices, int32_t ncore, int32_t nact, int32_t nvir, const int32_t* pairs,
+                              int32_t npairs, int32_t energy_only, int32_t* tiles, int32_t max_tiles);
+
+/* Spin limit (iterations of ~100 ns) of the eigensolver's grid barrier on
+ * the current device; spins <= 0 restores the default (about 2 s).  A tiny
+ * limit makes a multi-block solve's barrier wait run out, so that the
+ * solver returns DSRG_FNO_ERR_TIMEOUT (fault injection on the device without
+ * a hang: the expired block sets the status word and every block leaves). */
+int dsrg_fno_debug_set_barrier_limit(int64_t spins);
+
 /* Bytes of device workspace the single-instance calls hold on the current
  * device (grow-only; 0 before the first call and after dsrg_fno_release()).
  * Host only: reads the library's bookkeeping, launches nothing. */

@@ -34,6 +34,8 @@ EXPORTED = (
     "dsrg_fno_debug_regularizer",
     "dsrg_fno_debug_mma_schedule",
     "dsrg_fno_debug_workspace_bytes",
+    "dsrg_fno_debug_pair_tiles",
+    "dsrg_fno_debug_set_barrier_limit",
     "dsrg_fno_set_log_callback",
     "dsrg_fno_profile_enable",
     "dsrg_fno_profile_query",
@@ -113,6 +115,11 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_debug_regularizer.argtypes = [i32, dp, d, dp, dp]
     lib.dsrg_fno_debug_mma_schedule.argtypes = [i32, ctypes.POINTER(i32), i32]
     lib.dsrg_fno_debug_mma_schedule.restype = ctypes.c_int
+    lib.dsrg_fno_debug_pair_tiles.argtypes = [i32, i32, i32, i32, ctypes.POINTER(i32), i32, i32,
+                                              ctypes.POINTER(i32), i32]
+    lib.dsrg_fno_debug_pair_tiles.restype = ctypes.c_int
+    lib.dsrg_fno_debug_set_barrier_limit.argtypes = [ctypes.c_int64]
+    lib.dsrg_fno_debug_set_barrier_limit.restype = ctypes.c_int
     lib.dsrg_fno_debug_workspace_bytes.argtypes = []
     lib.dsrg_fno_debug_workspace_bytes.restype = ctypes.c_int64
     lib.dsrg_fno_set_log_callback.argtypes = [LOG_FN, vp]
@@ -336,3 +343,21 @@ def dsrg_fno_set_log_callback(fn=None):
     cb = LOG_FN(lambda level, msg, user: fn(int(level), msg.decode(errors="replace")))
     lib.dsrg_fno_set_log_callback(cb, None)
     _log_keep = cb
+
+
+def dsrg_fno_debug_pair_tiles(nslices, ncore, nact, nvir, pairs, energy_only=False):
+    """Output tiles (row tile, column tile) of the pair contraction for one
+    batch of hole pairs (host only)."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+    cap = max(16, 4 * len(pr) * ((nact + nvir) // 32 + 2) ** 2)
+    buf = np.zeros(2 * cap, dtype=np.int32)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    n = load().dsrg_fno_debug_pair_tiles(int(nslices), int(ncore), int(nact), int(nvir), pr.ctypes.data_as(ip),
+                                         len(pr) // 2, 1 if energy_only else 0, buf.ctypes.data_as(ip), cap)
+    _check("dsrg_fno_debug_pair_tiles", min(n, 0))
+    return [tuple(buf[2 * t:2 * t + 2]) for t in range(n)]
+
+
+def dsrg_fno_debug_set_barrier_limit(spins: int):
+    """Spin limit of the eigensolver's grid barrier (<= 0: default)."""
+    _check("dsrg_fno_debug_set_barrier_limit", load().dsrg_fno_debug_set_barrier_limit(int(spins)))

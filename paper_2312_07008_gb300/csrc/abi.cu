@@ -193,6 +193,10 @@ struct PassBuffers {
   float2* nu;        // double-float contraction tiles
   float2* eps_dd;    // orbital energies as double-float
   unsigned* rowmax;  // max |hi| per row of the dressed matrices (float bits)
+  int2* tiles;       // output tiles of the pair contraction, all batches
+  int* slot_of;      // [batch][nh][nh] slot of pair (i, j) in the batch, -1 outside
+  std::vector<long> tile_begin;
+  std::vector<int> tile_count;
 };
 
 // In the fast form tau, kappa and the dressed matrices are double-float
@@ -263,8 +267,8 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
     const Batch& b = P.batches[bi];
     double* ts = want_d ? W.ts : nullptr;
     if (W.ks) {
-      DSRG_TRY(sliced_pair_gemm(W.ks, g, W.planes_b, W.exps_b, W.kpad_q, W.pairs + b.pair_begin, b.npairs,
-                                ts == nullptr, W.nu, W.err, st));
+      DSRG_TRY(sliced_pair_gemm(W.ks, g, W.planes_b, W.exps_b, W.kpad_q, W.tiles + W.tile_begin[bi],
+                                W.tile_count[bi], W.slot_of + bi * (size_t)g.nh * g.nh, W.nu, W.err, st));
       DSRG_PHASE("phase_pair_epilogue", st);
       DSRG_TRY(pair_epilogue_dd(g, eps, W.eps_dd, W.pairs + b.pair_begin, b.npairs, W.nu, as_dd(W.tau),
                                 as_dd(W.kap), ts, st));
@@ -360,6 +364,9 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
     if (want_d)
       b += ws_bytes((size_t)ks * P.max_out * g.nv * pad64(g.nv), 2) + 2 * ws_bytes((size_t)P.max_out * g.nv, sizeof(int));
     b += ws_bytes(8, sizeof(int));
+    size_t tiles = 0;
+    for (const Batch& bt : P.batches) tiles += (size_t)pair_tile_bound(ks, g, bt.npairs);
+    b += ws_bytes(tiles + 1, sizeof(int2)) + ws_bytes(P.batches.size() * (size_t)g.nh * g.nh + 1, sizeof(int));
   }
   return b;
 }
@@ -409,6 +416,30 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
     W.err = ws_take<int>(ws, 8);
     if (!W.err) return DSRG_FNO_ERR_NOMEM;
     DSRG_CUDA(cudaMemsetAsync(W.err, 0, sizeof(int), st));
+    // output tiles and slot tables of every batch (host lists, one upload)
+    std::vector<int2> all, one;
+    std::vector<int> slots(P.batches.size() * (size_t)g.nh * g.nh, -1);
+    size_t bound = 0;
+    for (size_t bi = 0; bi < P.batches.size(); ++bi) {
+      const Batch& b = P.batches[bi];
+      bound += (size_t)pair_tile_bound(ks, g, b.npairs);
+      DSRG_TRY(pair_tiles(ks, g, P.pairs.data() + b.pair_begin, b.npairs, !want_d, one));
+      W.tile_begin.push_back((long)all.size());
+      W.tile_count.push_back((int)one.size());
+      all.insert(all.end(), one.begin(), one.end());
+      int* sl = slots.data() + bi * (size_t)g.nh * g.nh;
+      for (int k = 0; k < b.npairs; ++k) {
+        const int2 pr = P.pairs[b.pair_begin + k];
+        sl[(size_t)pr.x * g.nh + pr.y] = k;
+      }
+    }
+    W.tiles = ws_take<int2>(ws, bound + 1);
+    W.slot_of = ws_take<int>(ws, slots.size() + 1);
+    if (!W.slot_of || all.size() > bound) return DSRG_FNO_ERR_NOMEM;
+    if (!all.empty())
+      DSRG_CUDA(cudaMemcpyAsync(W.tiles, all.data(), all.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    if (!slots.empty())
+      DSRG_CUDA(cudaMemcpyAsync(W.slot_of, slots.data(), slots.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   }
   if (!P.pairs.empty())
     DSRG_CUDA(cudaMemcpyAsync(W.pairs, P.pairs.data(), P.pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, st));

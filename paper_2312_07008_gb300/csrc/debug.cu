@@ -115,3 +115,34 @@ extern "C" int64_t dsrg_fno_debug_workspace_bytes(void) {
   std::lock_guard<std::mutex> lk(workspace_mutex());
   return (int64_t)workspace_for_current_device().cap;
 }
+
+extern "C" int dsrg_fno_debug_pair_tiles(int32_t nslices, int32_t ncore, int32_t nact, int32_t nvir,
+                                         const int32_t* pairs, int32_t npairs, int32_t energy_only,
+                                         int32_t* tiles, int32_t max_tiles) {
+  if (nslices < 3 || nslices > 5 || ncore < 0 || nact < 0 || nvir <= 0 || ncore + nact <= 0 || npairs < 0 ||
+      (npairs > 0 && !pairs) || !tiles)
+    return DSRG_FNO_ERR_ARG;
+  Geometry g{};
+  g.nc = ncore;
+  g.na = nact;
+  g.nv = nvir;
+  g.nh = ncore + nact;
+  g.np = nact + nvir;
+  std::vector<int2> pr(npairs), out;
+  for (int k = 0; k < npairs; ++k) {
+    pr[k] = make_int2(pairs[2 * k], pairs[2 * k + 1]);
+    if (pr[k].x < 0 || pr[k].y < pr[k].x || pr[k].y >= g.nh) return DSRG_FNO_ERR_ARG;
+  }
+  DSRG_TRY(pair_tiles(nslices, g, pr.data(), npairs, energy_only != 0, out));
+  if ((long)out.size() > max_tiles || (long)out.size() > pair_tile_bound(nslices, g, npairs)) return DSRG_FNO_ERR_ARG;
+  for (size_t t = 0; t < out.size(); ++t) {
+    tiles[2 * t] = out[t].x;
+    tiles[2 * t + 1] = out[t].y;
+  }
+  return (int)out.size();
+}
+
+extern "C" int dsrg_fno_debug_set_barrier_limit(int64_t spins) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  return eig_set_barrier_limit((long long)spins);
+}

@@ -34,6 +34,9 @@ namespace {
 constexpr int JNT = JACOBI_THREADS;      // threads per block
 constexpr int JMAX_BLOCKS = EIG_MAX_BLOCKS;
 constexpr long long BAR_SPIN_LIMIT = 20000000;  // ~2 s of 100 ns naps
+// The grid barrier's spin limit on this device (a test hook may lower it to
+// make the wait run out; dsrg_fno_debug_set_barrier_limit).
+__device__ long long g_bar_spin_limit = BAR_SPIN_LIMIT;
 constexpr int SMEM_JACOBI_N = 80;               // largest n solved in shared memory (150 KB)
 
 // index at position pos of round r (position 0 fixed, the others rotate)
@@ -67,6 +70,7 @@ __device__ bool grid_barrier(const JacobiArgs& P) {
     const unsigned g = *gen;
     __threadfence();
     int ok = *st == 0;
+    const long long limit = g_bar_spin_limit;
     if (atomicAdd(P.bar, 1u) == gridDim.x - 1) {
       atomicExch(P.bar, 0u);
       __threadfence();
@@ -74,7 +78,7 @@ __device__ bool grid_barrier(const JacobiArgs& P) {
     } else {
       long long it = 0;
       while (ok && *gen == g) {
-        if (++it > BAR_SPIN_LIMIT || *st != 0) {
+        if (++it > limit || *st != 0) {
           atomicExch(P.status + 1, 1);
           ok = 0;
         }
@@ -389,6 +393,14 @@ SharedDeviceScope::~SharedDeviceScope() { t_device_shared = prev; }
 // A (n x n, symmetric) is destroyed: on return its diagonal holds the
 // eigenvalues; V (n x n) receives the eigenvectors (column j <-> A[j][j]).
 // work: eig_work_doubles(n) doubles.  status_dev: four ints of device memory.
+// Spin limit of the grid barrier on the current device; spins <= 0 restores
+// the default (test hook: a tiny limit makes the barrier's wait run out).
+int eig_set_barrier_limit(long long spins) {
+  const long long v = spins > 0 ? spins : BAR_SPIN_LIMIT;
+  DSRG_CUDA(cudaMemcpyToSymbol(g_bar_spin_limit, &v, sizeof(v)));
+  return DSRG_FNO_OK;
+}
+
 int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
                    cudaStream_t st) {
   if (n <= 0) return DSRG_FNO_OK;

@@ -71,6 +71,7 @@ int syrk_dressed_f64(int nv, int nr, const double* sig, const double* sig_sign, 
 // Symmetric-eigen helpers (eig.cu)
 constexpr int EIG_MAX_BLOCKS = 1024;  // grid bound of the eigensolver (reduction scratch)
 constexpr size_t eig_work_doubles(int n) { return 3 * (size_t)n * n + 2 * EIG_MAX_BLOCKS + 16; }
+int eig_set_barrier_limit(long long spins);
 int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
                    cudaStream_t st);
 // Marks the calling thread, for the scope's lifetime, as one of several host
@@ -114,8 +115,10 @@ int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int K
 // rowmax: NULL, or max |hi| per row as float bits (from dress_dd)
 int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
                   int* exps, const unsigned* rowmax, cudaStream_t st);
+int pair_tile_bound(int KS, const Geometry& g, int npairs);
+int pair_tiles(int KS, const Geometry& g, const int2* pairs, int npairs, bool energy_only, std::vector<int2>& out);
 int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
-                     const int2* pairs, int npairs, bool energy_only, float2* nu, int* err, cudaStream_t st);
+                     const int2* tiles, int ntiles, const int* slot_of, float2* nu, int* err, cudaStream_t st);
 // double-float elementwise stages (dd_stages.cu)
 int eps_to_dd(int n, const double* eps, float2* out, cudaStream_t st);
 int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd, const int2* pairs, int npairs,

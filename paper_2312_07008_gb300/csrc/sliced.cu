@@ -13,18 +13,17 @@
 // Every digit product is an integer of magnitude <= 2^14, so the level sums
 // S_0, S_1, S_2 over a chunk of 320 k-values stay below 3 * 320 * 2^14 < 2^24
 // in magnitude and the float32 accumulator of the tensor core holds them
-// exactly; they are merged after every chunk.  The levels L >= 3 carry
-// weights 2^-38 and smaller, so their float32 rounding (about 2^-24 of the
-// level) stays far below the digit truncation: they accumulate over the whole
-// contraction in TMEM and are merged once per tile (per segment in the
-// rank-K update).
+// exactly.  The levels L >= 3 carry weights 2^-38 and smaller, so their
+// float32 rounding (about 2^-24 of the level, 2^-48 of the product) stays far
+// below the digit truncation (2^-40).  Every level is merged after every
+// chunk, so the KS level accumulators of a chunk lie side by side in TMEM.
 //
 // Kernel.  Persistent, warp-specialised: warp 0 issues TMA loads of all KS
 // planes of a 64-wide k block (128-byte swizzle) into a 2-3 stage ring, warp 1
-// issues tcgen05.mma into per-level TMEM accumulators (levels 0-2 double
-// buffered per chunk, levels >= 3 double buffered per segment), warps 2-5
-// drain them with tcgen05.ld and add 2^-14-8L S_L into a float32-pair
-// (double-float) accumulator per element.  At the
+// issues tcgen05.mma into per-level TMEM accumulators (double buffered per
+// chunk; one MMA per A plane covers all its levels, the B planes being
+// stacked), warps 2-5 drain them with tcgen05.ld and add 2^-14-8L S_L into a
+// float32-pair (double-float) accumulator per element.  At the
 // end of a tile the float64 result is written out.  Every mbarrier wait is
 // bounded; on expiry the kernel records the failure and leaves.
 #include <cuda.h>
@@ -43,7 +42,6 @@ constexpr int BM = 128;
 constexpr int BKE = 64;            // k elements per block (128 bytes of bf16, 128-byte swizzle)
 constexpr int ROW_BYTES = 2 * BKE;
 constexpr int KCHUNK_BLOCKS = 320 / BKE;  // 320 k-values per exact sum of levels 0, 1, 2
-constexpr int NEXACT = kExactLevels;  // levels kept exact per chunk (3)
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
 
 enum { MODE_PAIR = 0, MODE_SYRK = 1, MODE_PLAIN = 2 };
@@ -218,9 +216,11 @@ struct GemmParams {
   int ntm, ntn;     // tiles along rows / columns
   int njobs;
   const int* exps;  // row exponents of the planes
-  // pair mode
-  const int2* pairs;
-  int np, na, energy_only;
+  // pair mode: output tiles of the (nh np) x (nh np) matrix of all hole-
+  // particle rows; element (i a, j b) goes to nu_out[slot_of[i nh + j]][a][b]
+  const int2* tiles;  // [njobs] (row tile, column tile)
+  const int* slot_of; // [nh nh], -1 for a pair outside the batch
+  int np, na, nh, rows;
   float2* nu_out;   // [slot][np][np], double-float
   // plain mode: C[m][n] = A[m] . B[n] (rows M x N), exps of A and B separately
   int M, N;
@@ -237,14 +237,10 @@ struct GemmParams {
 template <int BN>
 __device__ __forceinline__ bool decode_job(const GemmParams& P, int job, int* slot, int* mt, int* nt) {
   if (P.mode == MODE_PAIR) {
-    const int per = P.ntm * P.ntn;
-    *slot = job / per;
-    const int rem = job % per;
-    *mt = rem / P.ntn;
-    *nt = rem % P.ntn;
-    const int r0 = *mt * BM, c0 = *nt * BN;
-    if (r0 + BM <= P.na && c0 + BN <= P.na) return false;  // active x active only
-    if (P.energy_only && (r0 + BM <= P.na || c0 + BN <= P.na)) return false;
+    const int2 t = P.tiles[job];
+    *slot = 0;
+    *mt = t.x;
+    *nt = t.y;
     return true;
   }
   if (P.mode == MODE_PLAIN) {
@@ -289,7 +285,11 @@ struct Cfg {
   static_assert(SMEM <= 232448, "dynamic shared memory per block");
   static_assert((2 * STAGES + 9) * 8 + 8 <= 256, "barrier area");
   static constexpr int TMEM_COLS = 512;
-  static constexpr int SET_COLS = NEXACT * BN;              // exact levels of one chunk
+  // every level is accumulated per chunk and merged after it (levels 0-2
+  // exactly, see above), so one set of KS consecutive level accumulators,
+  // double buffered, and each A plane needs one MMA per k step
+  static constexpr int NEXACT = KS;
+  static constexpr int SET_COLS = NEXACT * BN;              // levels of one chunk
   static constexpr int TAIL_BASE = 2 * SET_COLS;             // lower levels of one segment
   static constexpr int TAIL_COLS = (KS - NEXACT) * BN;
   static_assert(2 * SET_COLS + 2 * (TAIL_COLS > 0 ? TAIL_COLS : 0) <= TMEM_COLS, "TMEM budget");
@@ -350,11 +350,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
         seg_range(P, slot, &r0, &r1);
         for (int r = r0; r < r1; ++r) {
           int arow, brow;
-          if (P.mode == MODE_PAIR) {
-            const int2 pr = P.pairs[slot];
-            arow = pr.x * P.np + mt * BM;
-            brow = pr.y * P.np + nt * BN;
-          } else if (P.mode == MODE_PLAIN) {
+          if (P.mode == MODE_PAIR || P.mode == MODE_PLAIN) {
             arow = mt * BM;
             brow = nt * BN;
           } else {
@@ -377,6 +373,14 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           if (*abort_flag) break;
         }
       }
+      // After an abort the MMA warp may not have consumed the last loads: no
+      // CTA leaves with bulk copies in flight, so wait (bounded) until the
+      // last load issued into every stage has landed.  Without an abort every
+      // load was consumed and this is skipped.
+      if (*abort_flag) {
+        for (uint32_t k = it > (uint32_t)STAGES ? it - STAGES : 0; k < it; ++k)
+          tc::mbar_wait(&full[k % STAGES], (k / STAGES) & 1, WAIT_LIMIT);
+      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
         for (int r = r0; r < r1 && !*abort_flag; ++r) {
           // low-order levels of this segment accumulate in tail set `lt`
           const uint32_t lt = segc & 1;
-          if (KS > NEXACT) {
+          if (KS > C::NEXACT) {
             if (!tc::mbar_wait(&lempty[lt], ((segc >> 1) & 1) ^ 1, WAIT_LIMIT)) {
               *abort_flag = 1;
               atomicExch(P.err, 5);
@@ -428,13 +432,13 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             // after another in TMEM, and the B planes lie one after another in
             // shared memory: one MMA with N = m.nb BN does them all.
 #pragma unroll
-            for (int i = 0; i < stacked_mma_count(KS, NEXACT); ++i) {
-              const StackedMma m = stacked_mma(KS, i, NEXACT);
+            for (int i = 0; i < stacked_mma_count(KS, C::NEXACT); ++i) {
+              const StackedMma m = stacked_mma(KS, i, C::NEXACT);
               // exact levels: per chunk (restart at the chunk's first block);
               // lower levels: per segment (restart at the segment's first block)
-              const bool exact = m.level < NEXACT;
+              const bool exact = m.level < C::NEXACT;
               const uint32_t d = exact ? tmem + set * C::SET_COLS + m.level * BN
-                                       : tmem + C::TAIL_BASE + lt * C::TAIL_COLS + (m.level - NEXACT) * BN;
+                                       : tmem + C::TAIL_BASE + lt * C::TAIL_COLS + (m.level - C::NEXACT) * BN;
               const bool first_block = exact ? (kc == 0) : (kb == 0);
               const uint32_t idesc = tc::make_idesc_bf16(BM, m.nb * BN);
 #pragma unroll
@@ -455,7 +459,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             }
           }
           if (*abort_flag) break;
-          if (KS > NEXACT) tc::mma_commit(&lfull[lt]);
+          if (KS > C::NEXACT) tc::mma_commit(&lfull[lt]);
           ++segc;
         }
       }
@@ -520,14 +524,14 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           }
           tc::tc_fence_after();
 #pragma unroll 1
-          for (int L = 0; L < NEXACT && L < KS; ++L) merge(L, set * C::SET_COLS + L * BN);
+          for (int L = 0; L < C::NEXACT && L < KS; ++L) merge(L, set * C::SET_COLS + L * BN);
           tc::tc_fence_before();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&tempty[set]);
           ++chunk;
         }
         if (failed) break;
-        if (KS > NEXACT) {
+        if (KS > C::NEXACT) {
           const uint32_t lt = segc & 1;
           if (!tc::mbar_wait(&lfull[lt], (segc >> 1) & 1, WAIT_LIMIT)) {
             *abort_flag = 1;
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           }
           tc::tc_fence_after();
 #pragma unroll 1
-          for (int L = NEXACT; L < KS; ++L) merge(L, C::TAIL_BASE + lt * C::TAIL_COLS + (L - NEXACT) * BN);
+          for (int L = C::NEXACT; L < KS; ++L) merge(L, C::TAIL_BASE + lt * C::TAIL_COLS + (L - C::NEXACT) * BN);
           tc::tc_fence_before();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&lempty[lt]);
@@ -547,17 +551,25 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
       if (failed) break;
       // ------------------------------------------------------ tile output
       if (P.mode == MODE_PAIR) {
-        const int2 pr = P.pairs[slot];
-        const int a = mt * BM + row;
-        if (a < P.np) {
-          const int ea = P.exps[(long)pr.x * P.np + a];
-          float2* out = P.nu_out + ((long)slot * P.np + a) * P.np;
+        const int R = mt * BM + row;
+        if (R < P.rows) {
+          const int i = R / P.np, a = R - i * P.np;
+          const int ea = P.exps[R];
+          const int* srow = P.slot_of + (long)i * P.nh;
+          int j = (nt * BN) / P.np, b = nt * BN - j * P.np;
 #pragma unroll
           for (int c = 0; c < BN; ++c) {
-            const int b = nt * BN + c;
-            if (b < P.np && !(a < P.na && b < P.na)) {
-              const int sc = ea + P.exps[(long)pr.y * P.np + b];
-              out[b] = make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));  // double-float nu
+            if (j < P.nh) {
+              const int slot = srow[j];
+              if (slot >= 0 && !(a < P.na && b < P.na)) {
+                const int sc = ea + P.exps[nt * BN + c];
+                P.nu_out[((long)slot * P.np + a) * P.np + b] =
+                    make_float2(ldexpf(hi[c], sc), ldexpf(lo[c], sc));  // double-float nu
+              }
+            }
+            if (++b == P.np) {
+              b = 0;
+              ++j;
             }
           }
         }
@@ -660,13 +672,7 @@ int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kp
     // executed tensor-core flops of the output tiles: tiles x 2 BM BN Kpad x digit products
     long tiles = 0;
     if (P.mode == MODE_PAIR) {
-      const int per = P.ntm * P.ntn;
-      for (int t = 0; t < per; ++t) {
-        const int r0 = (t / P.ntn) * BM, c0 = (t % P.ntn) * BN;
-        bool skip = (r0 + BM <= P.na && c0 + BN <= P.na) || (P.energy_only && (r0 + BM <= P.na || c0 + BN <= P.na));
-        if (!skip) ++tiles;
-      }
-      tiles *= (long)(P.njobs / per);
+      tiles = P.njobs;
     } else if (P.mode == MODE_SYRK) {
       tiles = (long)P.njobs / P.nsplit * P.nr;  // every segment of every upper tile
     } else {
@@ -733,21 +739,89 @@ int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, in
   return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, rowmax, st);
 }
 
-// nu[slot][a][b] for the listed pairs from B planes ([KS][nh*np][Kpad]).
+// Output tiles of the pair contraction for one batch of hole pairs (i <= j).
+// The rows of all holes form one (nh np)-row operand, so tiles run across the
+// borders of the pairs' np x np blocks and no tile is padded to a block edge.
+// A tile is listed when it meets a block of the batch outside that block's
+// active x active corner (and, energy only, inside its virtual x virtual
+// part).  Order: bands of ROW_BAND row tiles; within a band, column tile
+// by column tile, the band's row tiles in turn, so that the CTAs running at
+// one time share their A tiles (the band) and each B tile serves the band.
+static constexpr int ROW_BAND = 8;
+
+int pair_tile_bound(int KS, const Geometry& g, int npairs) {
+  const int BN = tile_n_for(KS);
+  return npairs * (ceil_div(g.np, BM) + 1) * (ceil_div(g.np, BN) + 1);
+}
+
+int pair_tiles(int KS, const Geometry& g, const int2* pairs, int npairs, bool energy_only, std::vector<int2>& out) {
+  out.clear();
+  if (npairs <= 0) return DSRG_FNO_OK;
+  const int BN = tile_n_for(KS);
+  const long np = g.np, na = g.na;
+  const int lo = energy_only ? (int)na : 0;
+  int mt0 = 1 << 30, mt1 = -1;
+  for (int k = 0; k < npairs; ++k) {
+    mt0 = std::min<int>(mt0, (int)((pairs[k].x * np + lo) / BM));
+    mt1 = std::max<int>(mt1, (int)((pairs[k].x * np + np - 1) / BM));
+  }
+  const int ntt = ceil_div((long)g.nh * np, BN);
+  const int words = (ntt + 63) / 64;
+  std::vector<uint64_t> bits((size_t)(mt1 - mt0 + 1) * words, 0);
+  auto set_range = [&](int mt, int n0, int n1) {  // [n0, n1]
+    uint64_t* row = bits.data() + (size_t)(mt - mt0) * words;
+    for (int n = n0; n <= n1; ++n) row[n >> 6] |= (uint64_t)1 << (n & 63);
+  };
+  for (int k = 0; k < npairs; ++k) {
+    const long i = pairs[k].x, j = pairs[k].y;
+    const long r0 = i * np + lo, r1 = i * np + np, c0 = j * np + lo, c1 = j * np + np;
+    for (int mt = (int)(r0 / BM); mt <= (int)((r1 - 1) / BM); ++mt) {
+      // rows of this tile inside the block all active: skip the column
+      // tiles that stay inside the active columns
+      const bool rows_active = std::min<long>((long)mt * BM + BM, r1) - i * np <= na;
+      long cs = c0;
+      if (rows_active) {
+        const long first = (j * np + na) / BN;  // first column tile reaching a virtual column
+        cs = std::max<long>(c0, first * BN);
+      }
+      if (cs >= c1) continue;
+      set_range(mt, (int)(cs / BN), (int)((c1 - 1) / BN));
+    }
+  }
+  std::vector<uint64_t> band(words);
+  for (int b0 = mt0; b0 <= mt1; b0 += ROW_BAND) {
+    const int b1 = std::min(mt1, b0 + ROW_BAND - 1);
+    std::fill(band.begin(), band.end(), 0);
+    for (int mt = b0; mt <= b1; ++mt)
+      for (int w = 0; w < words; ++w) band[w] |= bits[(size_t)(mt - mt0) * words + w];
+    for (int w = 0; w < words; ++w) {
+      uint64_t m = band[w];
+      while (m) {
+        const int n = w * 64 + __builtin_ctzll(m);
+        m &= m - 1;
+        for (int mt = b0; mt <= b1; ++mt)
+          if ((bits[(size_t)(mt - mt0) * words + (n >> 6)] >> (n & 63)) & 1) out.push_back(make_int2(mt, n));
+      }
+    }
+  }
+  return DSRG_FNO_OK;
+}
+
+// nu[slot][a][b] of a batch of pairs from B planes ([KS][nh*np][Kpad]) over
+// the output tiles of pair_tiles (device copy) and the batch's slot table.
 int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
-                     const int2* pairs, int npairs, bool energy_only, float2* nu, int* err, cudaStream_t st) {
+                     const int2* tiles, int ntiles, const int* slot_of, float2* nu, int* err, cudaStream_t st) {
   GemmParams P{};
   P.mode = MODE_PAIR;
   P.nkb = Kpad / BKE;
-  const int BN = tile_n_for(KS);
-  P.ntm = ceil_div(g.np, BM);
-  P.ntn = ceil_div(g.np, BN);
-  P.njobs = npairs * P.ntm * P.ntn;
+  P.njobs = ntiles;
   P.exps = exps;
-  P.pairs = pairs;
+  P.tiles = tiles;
+  P.slot_of = slot_of;
   P.np = g.np;
   P.na = g.na;
-  P.energy_only = energy_only ? 1 : 0;
+  P.nh = g.nh;
+  P.rows = g.nh * g.np;
   P.nu_out = nu;
   P.err = err;
   const long rows = (long)g.nh * g.np;

@@ -86,3 +86,22 @@ def test_diagonal_input_needs_no_rotation():
     ons, nos = solve(np.diag(lam))
     np.testing.assert_array_equal(ons, np.sort(lam)[::-1])
     assert np.abs(np.abs(nos).sum(axis=0) - 1.0).max() == 0.0
+
+
+def test_grid_barrier_timeout_is_reported_and_the_next_solve_is_clean():
+    """Fault injection without a hang: with the grid barrier's spin limit
+    lowered to one nap, a multi-block solve (n > 80) has a barrier wait run
+    out; the expired block sets the status word, every block leaves, and the
+    call returns DSRG_FNO_ERR_TIMEOUT.  The context stays usable: with the
+    default limit restored the same call succeeds and matches LAPACK."""
+    rng = np.random.default_rng(91)
+    D = with_spectrum(rng, np.linspace(2.0, 0.01, 300))
+    pkg.dsrg_fno_debug_set_barrier_limit(1)
+    try:
+        with pytest.raises(pkg.DsrgFnoError) as ei:
+            solve(D)
+        assert ei.value.status == -5
+    finally:
+        pkg.dsrg_fno_debug_set_barrier_limit(0)
+    ons, nos = solve(D)
+    check(D, ons, nos)
