@@ -484,6 +484,38 @@ def discarded_correction(prob, no, nkept, e_mo=None):
     return e_mo - e_fno, e_fno, eps_new
 
 
+# --------------------------------------------------------------------------
+# Natural auxiliary functions (Sec. 4: compression of the auxiliary basis)
+# --------------------------------------------------------------------------
+def naf(prob, threshold):
+    """Natural auxiliary functions of the hole-particle DF factors.
+
+    W_PQ = sum_{i a} B^P_{ia} B^Q_{ia} (i hole, a particle) is diagonalised,
+    W = U diag(w) U^T with w descending; the natural auxiliary functions
+    are the columns of U with w > threshold, and the compressed factors are
+    B'^K_{ia} = sum_Q U_QK B^Q_{ia}.  Returns (B' [k][nh][np], w, U)."""
+    nq = prob.naux
+    B2 = prob.B.reshape(nq, -1)
+    W = B2 @ B2.T
+    w, U = np.linalg.eigh(W)
+    order = np.argsort(-w, kind="stable")
+    w, U = w[order], U[:, order]
+    k = int(np.count_nonzero(w > threshold))
+    Bp = (U[:, :k].T @ B2).reshape((k,) + prob.B.shape[1:])
+    return Bp, w, U
+
+
+def naf_problem(prob, threshold):
+    """The same problem with B replaced by its natural-auxiliary-function
+    compression (naux -> the number of kept functions)."""
+    from copy import copy
+    Bp, _, _ = naf(prob, threshold)
+    p2 = copy(prob)
+    p2.B = np.ascontiguousarray(Bp)
+    p2.naux = Bp.shape[0]
+    return p2
+
+
 def solve(prob, cuts=(98.5,), mode=MODE_PO, degen_ratio=0.01):
     """The whole path: E_vv, D_vv, NOs/ONs, N' per cut, correction per cut."""
     e2 = e_vv(prob)

@@ -567,3 +567,47 @@ def test_sampling_restrictions_partition_terms_4_5_7():
         ref = full[term]
         assert np.max(np.abs(parts[0] + parts[1] - ref)) <= 1e-13 * np.max(np.abs(ref))
         assert np.max(np.abs(O.dvv_terms(p, terms=(term,), **{key: []})[term])) == 0.0
+
+
+# ------------------------------------------------- natural auxiliary functions
+def test_naf_spectrum_is_the_squared_singular_values():
+    """W = B B^T over the hole-particle pairs: its eigenvalues are the squared
+    singular values of B as a naux x (nh np) matrix (LAPACK SVD)."""
+    p = make_problem(ncore=3, nact=2, nvir=13, naux=31, seed=81, nstates=2)
+    _, w, U = O.naf(p, -1.0)
+    sv = np.linalg.svd(p.B.reshape(p.naux, -1), compute_uv=False)
+    assert np.allclose(w, sv ** 2, rtol=1e-12, atol=1e-14 * sv[0] ** 2)
+    assert np.allclose(U.T @ U, np.eye(p.naux), atol=1e-13)
+
+
+def test_naf_keeping_every_function_changes_nothing():
+    """With every function kept, B' is an orthogonal rotation of the
+    auxiliary index, under which nu = B^T B, hence E_vv and D_vv, are exact
+    invariants."""
+    p = make_problem(ncore=3, nact=2, nvir=13, naux=31, seed=82, nstates=2)
+    q = O.naf_problem(p, -1.0)
+    assert q.naux == p.naux
+    assert abs(O.e_vv(q) - O.e_vv(p)) <= 1e-12 * abs(O.e_vv(p))
+    d0, d1 = O.dvv(p), O.dvv(q)
+    assert np.max(np.abs(d1 - d0)) <= 1e-12 * np.max(np.abs(d0))
+
+
+def test_naf_discarded_weight_and_integral_error():
+    """Truncation to the functions with w > threshold: the projected-out part
+    of the factors has squared norm sum_{discarded} w (the eigen-decomposition
+    written as a sum of squares), and every integral nu^{ij}_{ab} changes by at
+    most |B_ia - P B_ia| |B_jb - P B_jb| (Cauchy-Schwarz)."""
+    p = make_problem(ncore=3, nact=2, nvir=13, naux=31, seed=83, nstates=2)
+    _, w, U = O.naf(p, -1.0)
+    thr = w[20]
+    Bp, _, _ = O.naf(p, thr)
+    k = Bp.shape[0]
+    assert k == 20
+    B2 = p.B.reshape(p.naux, -1)
+    P = U[:, :k] @ U[:, :k].T
+    R = B2 - P @ B2
+    assert abs(np.sum(R * R) - np.sum(w[k:])) <= 1e-10 * np.sum(w)
+    nu = B2.T @ B2
+    nup = Bp.reshape(k, -1).T @ Bp.reshape(k, -1)
+    rn = np.sqrt(np.sum(R * R, axis=0))
+    assert np.all(np.abs(nu - nup) <= np.outer(rn, rn) * (1 + 1e-9) + 1e-14)
