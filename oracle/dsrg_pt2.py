@@ -485,6 +485,21 @@ def discarded_correction(prob, no, nkept, e_mo=None):
 
 
 # --------------------------------------------------------------------------
+# Particle-particle ladder of Eq. 6 in the truncated virtual basis
+# --------------------------------------------------------------------------
+def ladder(B_vv, T):
+    """The term of C2 = [O2, T2]_2 (Eq. 6) with four virtual indices, whose
+    O(N_C^2 N_V^4) cost the FNO truncation cuts by (N_V'/N_V)^4:
+        C^{ij}_{ab} = sum_{cd} <ab|cd> T^{ij}_{cd},
+        <ab|cd> = (ac|bd) = sum_Q B^Q_{ac} B^Q_{bd}   (DF, Sec. 3).
+    B_vv [naux][nv][nv] virtual-virtual factors, T [npairs][nv][nv]
+    (T[p][c][d] = T^{ij}_{cd} of hole pair p); returns C [npairs][nv][nv].
+    The 4-index integrals are formed explicitly (plain definition)."""
+    V = np.einsum("Qac,Qbd->abcd", B_vv, B_vv, optimize=True)
+    return np.einsum("abcd,pcd->pab", V, T, optimize=True)
+
+
+# --------------------------------------------------------------------------
 # Natural auxiliary functions (Sec. 4: compression of the auxiliary basis)
 # --------------------------------------------------------------------------
 def naf(prob, threshold):

@@ -611,3 +611,49 @@ def test_naf_discarded_weight_and_integral_error():
     nup = Bp.reshape(k, -1).T @ Bp.reshape(k, -1)
     rn = np.sqrt(np.sum(R * R, axis=0))
     assert np.all(np.abs(nu - nup) <= np.outer(rn, rn) * (1 + 1e-9) + 1e-14)
+
+
+# ------------------------------------------------ particle-particle ladder
+def test_ladder_against_explicit_loops():
+    rng = np.random.default_rng(95)
+    nq, nv, npairs = 4, 5, 3
+    Bv = rng.standard_normal((nq, nv, nv))
+    T = rng.standard_normal((npairs, nv, nv))
+    C = O.ladder(Bv, T)
+    ref = np.zeros_like(C)
+    for p_ in range(npairs):
+        for a in range(nv):
+            for b in range(nv):
+                s = 0.0
+                for c in range(nv):
+                    for d in range(nv):
+                        v = sum(Bv[q, a, c] * Bv[q, b, d] for q in range(nq))
+                        s += v * T[p_, c, d]
+                ref[p_, a, b] = s
+    assert np.max(np.abs(C - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_ladder_is_covariant_under_virtual_rotation():
+    """Rotating the virtual basis (B'^Q = U^T B^Q U, T' = U^T T U for every
+    pair) rotates the result the same way, C' = U^T C U."""
+    rng = np.random.default_rng(96)
+    nq, nv, npairs = 7, 9, 4
+    Bv = rng.standard_normal((nq, nv, nv))
+    Bv = Bv + Bv.transpose(0, 2, 1)
+    T = rng.standard_normal((npairs, nv, nv))
+    U, _ = np.linalg.qr(rng.standard_normal((nv, nv)))
+    C = O.ladder(Bv, T)
+    C2 = O.ladder(np.einsum("ea,Qef,fb->Qab", U, Bv, U), np.einsum("ca,pcd,db->pab", U, T, U))
+    assert np.max(np.abs(C2 - np.einsum("ea,pef,fb->pab", U, C, U))) <= 1e-12 * np.max(np.abs(C))
+
+
+def test_ladder_pair_transpose_symmetry():
+    """With symmetric factors (B^Q_{ac} = B^Q_{ca}) the integrals satisfy
+    <ab|cd> = <ba|dc>, so T^{ji} = (T^{ij})^T gives C^{ji} = (C^{ij})^T."""
+    rng = np.random.default_rng(97)
+    nq, nv = 6, 8
+    Bv = rng.standard_normal((nq, nv, nv))
+    Bv = Bv + Bv.transpose(0, 2, 1)
+    t = rng.standard_normal((nv, nv))
+    C = O.ladder(Bv, np.stack([t, t.T]))
+    assert np.max(np.abs(C[1] - C[0].T)) <= 1e-12 * np.max(np.abs(C))
