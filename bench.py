@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--nslices", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the float64 GPU form (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the sub-results (CAS(12,12) workload and the 64-instance batch)")
+    ap.add_argument("--fused-epilogue", action="store_true",
+                    help="run the Eq. A7 regulariser in the contraction kernel (comparison with the separate default)")
     return ap.parse_args()
 
 
@@ -479,6 +483,7 @@ def main():
     p = workload(args.workload)
     cuts = cuts_of(args.workload)
     nv = p.nvir
+    pkg.dsrg_fno_debug_set_fused_epilogue(args.fused_epilogue)
     dev = torch.device("cuda", local)
     gp = pkg.problem_from_synth(p, dev, pkg.SLICED_BF16, args.nslices)
     d = torch.empty((nv, nv), dtype=torch.float64, device=dev)
@@ -584,7 +589,8 @@ def main():
                              "ms_per_step": f64_ms / args.fp64_steps,
                              "peak": PEAKS_OWN["fp64_dgemm_tflops"],
                              "peak_kind": "cuBLAS float64 GEMM (torch.matmul), measured by this repository",
-                             "frac": (f64_tf / PEAKS_OWN["fp64_dgemm_tflops"]) if f64_tf else None,
+                             "frac": (f64_tf / PEAKS_OWN["fp64_dgemm_tflops"])
+                             if (f64_tf and PEAKS_OWN["fp64_dgemm_tflops"]) else None,
                              "frac_of_nominal": (f64_tf / 1.25) if f64_tf else None,
                              "nominal_tflops": 1.25},
                 "fast_minus_fp64": {"e2": res["e2"] - r64["e2"],
@@ -599,7 +605,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": f"bf16 digit planes (k={args.nslices}) -> exact f32 level sums -> f64",
         "data": "synthetic",
-        "config": single_config(p, args.workload, cuts, args.nslices),
+        "config": dict(single_config(p, args.workload, cuts, args.nslices),
+                       epilogue="fused" if args.fused_epilogue else "separate kernel"),
         "gflops": flops * value / 1e9,
         "s_per_solve": ms_max / args.steps / 1e3,
         "roofline": roofline,
@@ -611,12 +618,80 @@ def main():
         "result": {"e2": res["e2"], **{f"nkept_{c}": res[c][0] for c in cuts}, **{f"de_{c}": res[c][1] for c in cuts},
                    "cut_margins": [cut_margins(ons_last, c, res[c][0]) for c in cuts]},
     }
+    if not args.no_sub:
+        line["sub_results"] = sub_results(pkg, dev, args.nslices)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, [res[c][0] for c in cuts])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+SUB_SINGLE = "sa_cas12_ncore95_nvir1000_naux4200"
+
+
+def sub_results(pkg, dev, nslices, steps=3, warmup=2):
+    """The other two measured workloads, timed after the headline one:
+    the CAS(12,12) ncore 95 / nvir 1000 / naux 4200 solve (fast form) and
+    the 64-instance ragged batch through dsrg_fno_batch_run."""
+    import torch
+    from synth import workload
+    from synth.problems import batch_sizes, batch_problem
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n, r
+
+    p = workload(SUB_SINGLE)
+    cuts = cuts_of(SUB_SINGLE)
+    nv = p.nvir
+    gp = pkg.problem_from_synth(p, dev, pkg.SLICED_BF16, nslices)
+    d = torch.empty((nv, nv), dtype=torch.float64, device=dev)
+    on = torch.empty(nv, dtype=torch.float64, device=dev)
+    no = torch.empty((nv, nv), dtype=torch.float64, device=dev)
+
+    def one():
+        e2 = pkg.dsrg_fno_vv_opdm(gp, d)
+        res = {"e2": e2}
+        for i, c in enumerate(cuts):
+            k = (pkg.dsrg_fno_truncate(nv, d, pkg.MODE_PO, c, 0.01, on, no) if i == 0
+                 else pkg.dsrg_fno_cut(nv, on, pkg.MODE_PO, c, 0.01))
+            res[c] = (k, pkg.dsrg_fno_discarded_correction(gp, k, no, e2_mo=e2)[0])
+        return res
+
+    for _ in range(warmup):
+        one()
+    ms, r = timed(one, steps)
+    out[SUB_SINGLE] = {"s_per_solve": ms / 1e3, "solves_per_s": 1e3 / ms,
+                       "gflops": algorithmic_flops(p) / (ms / 1e3) / 1e9, "steps": steps, "warmup": warmup,
+                       "e2": r["e2"], **{f"nkept_{c}": r[c][0] for c in cuts}, **{f"de_{c}": r[c][1] for c in cuts},
+                       "cut_margins": [cut_margins(on.cpu().numpy(), c, r[c][0]) for c in cuts]}
+    del gp, d, on, no
+    sizes = batch_sizes()
+    probs = [batch_problem(k) for k in range(len(sizes))]
+    gps = [pkg.problem_from_synth(q, dev, pkg.SLICED_BF16, nslices) for q in probs]
+    dvv = [torch.empty((q.nvir, q.nvir), dtype=torch.float64, device=dev) for q in probs]
+    ons = [torch.empty(q.nvir, dtype=torch.float64, device=dev) for q in probs]
+    nos = [torch.empty((q.nvir, q.nvir), dtype=torch.float64, device=dev) for q in probs]
+    cut = (pkg.MODE_PO, BATCH_CUT, 0.01)
+    run = lambda: pkg.dsrg_fno_batch_run(gps, dvv, cut, ons, nos, correction=True, nworkers=0)  # noqa: E731
+    for _ in range(max(warmup, 4)):   # the first calls try 2, 4 and 8 workers
+        run()
+    ms, r = timed(run, steps)
+    out[BATCH_WORKLOAD] = {"s_per_batch": ms / 1e3, "instances_per_s": len(probs) / (ms / 1e3),
+                           "gflops": sum(algorithmic_flops(q) for q in probs) / (ms / 1e3) / 1e9,
+                           "workers": pkg.dsrg_fno_batch_last_workers(), "steps": steps,
+                           "sum_e2": sum(x["e2"] for x in r), "sum_nkept": sum(x["nkept"] for x in r)}
+    return out
 
 
 # DRAM bytes per executed flop of the pair contraction, from one ncu capture
@@ -654,7 +729,7 @@ def traffic_per_launch(workload, exec_flops_per_launch):
 # only): cuBLAS float64 and TF32 GEMMs through torch.matmul, n = 8192, best
 # of several, CUDA events; the command and the clocks are in
 # profiles/peaks_fp64_tf32_gb300.md.
-PEAKS_OWN = {"fp64_dgemm_tflops": None, "tf32_tflops": None}
+PEAKS_OWN = {"fp64_dgemm_tflops": 1.0988, "tf32_tflops": 1027.07}
 
 
 def roofline_of(pair_ms, pair_n, pair_fl, syrk, plain, step_ms, workload=None, alg_flops=None, nslices=5):

@@ -55,7 +55,19 @@ typedef enum {
  * and D_vv sums in float64.  In both forms the NO eigensolve runs in
  * double-float.  On the workloads here the two forms agree to a few 1e-9 E_h
  * in energies; ONs are tested to agree within 1e-8. */
-typedef enum { DSRG_FNO_FP64 = 0, DSRG_FNO_SLICED_BF16 = 1 } dsrg_fno_precision;
+/* BF16X3 and TF32 are the literal forms of the precision study: only the
+ * contractions of B with B (nu^{ij}_{ab} = sum_Q B^Q_{ia} B^Q_{jb}, Eq. A7, of
+ * the D_vv pass and of the energy passes of the correction) run as tensor-
+ * core products with one float32 accumulator over the whole auxiliary index;
+ * everything else runs as in SLICED_BF16 with 5 planes.
+ *   BF16X3: x = hi + lo (hi = bf16(x), lo = bf16(x - hi)), products
+ *           hi.hi + hi.lo + lo.hi (3 terms).
+ *   TF32:   nslices 1: tf32(x).tf32(y); nslices 0 or 3: x = big + small
+ *           (tf32 parts), big.big + big.small + small.big (3 terms).
+ * Their errors against float64 are far above 1e-7 E_h on the workloads here
+ * (they exist to measure that); SLICED_BF16 is the fast form. */
+typedef enum { DSRG_FNO_FP64 = 0, DSRG_FNO_SLICED_BF16 = 1, DSRG_FNO_BF16X3 = 2, DSRG_FNO_TF32 = 3 }
+    dsrg_fno_precision;
 
 typedef struct {
   int32_t ncore, nact, nvir, naux;
@@ -82,6 +94,7 @@ typedef struct {
   double s;
   int32_t precision;  /* dsrg_fno_precision */
   int32_t nslices;    /* SLICED_BF16 digit planes: 3, 4 or 5; 0 = library default (5);
+                       * TF32 terms: 1 or 3 (0 = 3); BF16X3: 0 or 3;
                        * other values give DSRG_FNO_ERR_UNSUPPORTED */
 } dsrg_fno_problem;
 
@@ -189,6 +202,47 @@ int dsrg_fno_cut(int32_t nvir, const double* ons, int32_t mode, double threshold
 int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_t mode, double threshold,
                               double degen_ratio, double* on_out, double* no_out,
                               int32_t* nkept_out, void* stream);
+
+/* Particle-particle ladder of Eq. 6 in a (truncated) virtual basis: of the
+ * two-body commutator C2 = [O2, T2]_2, the term with four virtual indices,
+ * which sets its O(N_C^2 N_V^4) cost and which the FNO truncation cuts by
+ * (N_V'/N_V)^4 (Sec. 2):
+ *   C^{ij}_{ab} = sum_{cd} <ab|cd> T^{ij}_{cd},  <ab|cd> = sum_Q B^Q_{ac} B^Q_{bd}
+ * with the bare DF integrals as the four-virtual block of O2.
+ *   nv, naux   virtual orbitals of the basis (N_V or N_V') and DF functions.
+ *   B_vv       device [naux][nv][nv]: B^Q_{ab}, virtual-virtual DF factors in
+ *              that basis (e.g. rotated to the recanonicalised kept NOs).
+ *   T          device [npairs][nv][nv]: T[p][c][d] = T^{ij}_{cd} of hole pair p.
+ *   precision  DSRG_FNO_FP64 or DSRG_FNO_SLICED_BF16 (5 digit planes).
+ *   C_out      device [npairs][nv][nv].
+ * The 4-index integrals are formed for 8 values of a at a time and never
+ * stored whole.  Errors: DSRG_FNO_ERR_ARG for bad sizes, null or host
+ * pointers; sizes with nv^3 * 8 or npairs * nv^2 >= 2^31 and other
+ * precisions give DSRG_FNO_ERR_UNSUPPORTED. */
+int dsrg_fno_ladder(int32_t nv, int32_t naux, const double* B_vv, int32_t npairs, const double* T,
+                    int32_t precision, double* C_out, void* stream);
+
+/* Natural auxiliary functions (the compression of the auxiliary basis that
+ * Sec. 4 proposes for the PT2 step): W_PQ = sum_{ia} B^P_{ia} B^Q_{ia} over
+ * the hole-particle factors is diagonalised, W = U diag(w) U^T with w
+ * descending, and the factors are rotated to the naux' eigenvectors with
+ * w_K > threshold: B'^K_{ia} = sum_Q U_QK B^Q_{ia}.  B' gives every integral
+ * nu^{ij}_{ab} up to the discarded weight (sum of the dropped w), so a
+ * problem with B' and naux' replaces the original one.
+ *   nh, np     holes (ncore + nact) and particles (nact + nvir).
+ *   B_hp       device [naux][nh][np], as in dsrg_fno_problem.
+ *   threshold  absolute eigenvalue threshold (w > threshold kept).
+ *   precision  DSRG_FNO_FP64, or DSRG_FNO_SLICED_BF16 (digit-plane
+ *              contractions: 5 planes for W, 6 for B'); the eigensolve is the
+ *              double-float Jacobi solver in both.
+ *   B_out      device [naux][nh][np], caller-allocated: its first naux'
+ *              slices receive B' (the rest is left untouched).
+ *   w_out      device [naux] or NULL: every eigenvalue of W, descending.
+ *   naux_out   host: naux'.
+ * Errors: DSRG_FNO_ERR_ARG for bad sizes, null or host pointers; other
+ * precisions give DSRG_FNO_ERR_UNSUPPORTED. */
+int dsrg_fno_naf(int32_t nh, int32_t np, int32_t naux, const double* B_hp, double threshold,
+                 int32_t precision, double* B_out, double* w_out, int32_t* naux_out, void* stream);
 
 /* Second-order correction for the discarded virtuals (scalar part of
  * Eq. 11): the kept NOs (first nkept columns of `no`, device [nvir][nvir])

@@ -20,6 +20,13 @@ extern "C" {
 int dsrg_fno_debug_sliced_gemm(int32_t nslices, int32_t M, int32_t N, int32_t K, const double* A,
                                const double* B, double* C);
 
+/* C[M][N] = A[M][K] B[N][K]^T in a literal form of the precision study
+ * (precision DSRG_FNO_BF16X3, nterms 0 or 3; DSRG_FNO_TF32, nterms 1 or 3,
+ * 0 = 3): split parts on the tensor cores, one float32 accumulator over K.
+ * Host float64 arrays, row-major. */
+int dsrg_fno_debug_literal_gemm(int32_t precision, int32_t nterms, int32_t M, int32_t N, int32_t K,
+                                const double* A, const double* B, double* C);
+
 /* Digit planes of rows[R][K] (host float64): planes[s][r][Kpad] as float
  * values (host, R*Kpad*nslices) and the row exponents exps[R] (host). */
 int dsrg_fno_debug_slice_rows(int32_t nslices, int32_t R, int32_t K, const double* rows, float* planes,
@@ -59,6 +66,12 @@ int dsrg_fno_debug_pair_tiles(int32_t nslices, int32_t ncore, int32_t nact, int3
  * solver returns DSRG_FNO_ERR_TIMEOUT (fault injection on the device without
  * a hang: the expired block sets the status word and every block leaves). */
 int dsrg_fno_debug_set_barrier_limit(int64_t spins);
+
+/* on != 0: the fast form's Eq. A7 regulariser runs in the output stage of
+ * the pair-contraction kernel; 0 (the default, faster on GB300): in a
+ * separate kernel over the stored contraction tiles.  Affects later calls of
+ * this process. */
+int dsrg_fno_debug_set_fused_epilogue(int32_t on);
 
 /* Bytes of device workspace the single-instance calls hold on the current
  * device (grow-only; 0 before the first call and after dsrg_fno_release()).

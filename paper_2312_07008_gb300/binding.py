@@ -23,12 +23,15 @@ EXPORTED = (
     "dsrg_fno_truncate",
     "dsrg_fno_truncate_noalloc",
     "dsrg_fno_cut",
+    "dsrg_fno_naf",
+    "dsrg_fno_ladder",
     "dsrg_fno_discarded_correction",
     "dsrg_fno_sa_densities",
     "dsrg_fno_batch_run",
     "dsrg_fno_status_string",
     "dsrg_fno_release",
     "dsrg_fno_debug_sliced_gemm",
+    "dsrg_fno_debug_literal_gemm",
     "dsrg_fno_debug_slice_rows",
     "dsrg_fno_debug_slice_rows_dd",
     "dsrg_fno_debug_regularizer",
@@ -36,6 +39,7 @@ EXPORTED = (
     "dsrg_fno_debug_workspace_bytes",
     "dsrg_fno_debug_pair_tiles",
     "dsrg_fno_debug_set_barrier_limit",
+    "dsrg_fno_debug_set_fused_epilogue",
     "dsrg_fno_set_log_callback",
     "dsrg_fno_profile_enable",
     "dsrg_fno_profile_query",
@@ -45,6 +49,8 @@ EXPORTED = (
 
 FP64 = 0
 SLICED_BF16 = 1
+BF16X3 = 2
+TF32 = 3
 MODE_PO, MODE_PV, MODE_NKAPPA, MODE_FIXED = 0, 1, 2, 3
 
 
@@ -96,6 +102,8 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_truncate.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_truncate_noalloc.argtypes = [i32, vp, i32, d, d, vp, vp, ctypes.POINTER(i32), vp]
     lib.dsrg_fno_cut.argtypes = [i32, vp, i32, d, d, ctypes.POINTER(i32), vp]
+    lib.dsrg_fno_naf.argtypes = [i32, i32, i32, vp, d, i32, vp, vp, ctypes.POINTER(i32), vp]
+    lib.dsrg_fno_ladder.argtypes = [i32, i32, vp, i32, vp, i32, vp, vp]
     lib.dsrg_fno_discarded_correction.argtypes = [P, i32, vp, ctypes.POINTER(d), ctypes.POINTER(d),
                                                   ctypes.POINTER(d), vp, vp]
     dp_ = ctypes.POINTER(d)
@@ -108,6 +116,8 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_release.argtypes = []
     dp = ctypes.POINTER(d)
     lib.dsrg_fno_debug_sliced_gemm.argtypes = [i32, i32, i32, i32, dp, dp, dp]
+    lib.dsrg_fno_debug_literal_gemm.argtypes = [i32, i32, i32, i32, i32, dp, dp, dp]
+    lib.dsrg_fno_debug_literal_gemm.restype = ctypes.c_int
     lib.dsrg_fno_debug_slice_rows.argtypes = [i32, i32, i32, dp, ctypes.POINTER(ctypes.c_float),
                                               ctypes.POINTER(i32)]
     lib.dsrg_fno_debug_slice_rows_dd.argtypes = [i32, i32, i32, ctypes.POINTER(ctypes.c_float),
@@ -118,6 +128,8 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_debug_pair_tiles.argtypes = [i32, i32, i32, i32, ctypes.POINTER(i32), i32, i32,
                                               ctypes.POINTER(i32), i32]
     lib.dsrg_fno_debug_pair_tiles.restype = ctypes.c_int
+    lib.dsrg_fno_debug_set_fused_epilogue.argtypes = [i32]
+    lib.dsrg_fno_debug_set_fused_epilogue.restype = ctypes.c_int
     lib.dsrg_fno_debug_set_barrier_limit.argtypes = [ctypes.c_int64]
     lib.dsrg_fno_debug_set_barrier_limit.restype = ctypes.c_int
     lib.dsrg_fno_debug_workspace_bytes.argtypes = []
@@ -132,7 +144,7 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_launch_count.restype = ctypes.c_int64
     for f in ("dsrg_fno_pt2_energy", "dsrg_fno_vv_opdm", "dsrg_fno_vv_opdm_lambda3", "dsrg_fno_sa_lambda3",
               "dsrg_fno_truncate", "dsrg_fno_truncate_noalloc",
-              "dsrg_fno_cut", "dsrg_fno_discarded_correction", "dsrg_fno_sa_densities", "dsrg_fno_batch_run"):
+              "dsrg_fno_cut", "dsrg_fno_naf", "dsrg_fno_ladder", "dsrg_fno_discarded_correction", "dsrg_fno_sa_densities", "dsrg_fno_batch_run"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -228,6 +240,22 @@ def dsrg_fno_cut(nvir, ons, mode, threshold, degen_ratio, stream=None) -> int:
     _check("dsrg_fno_cut", load().dsrg_fno_cut(nvir, _ptr(ons), mode, float(threshold), float(degen_ratio),
                                               ctypes.byref(k), _stream(stream)))
     return k.value
+
+
+def dsrg_fno_naf(nh, np_, naux, B, threshold, precision, B_out, w_out=None, stream=None) -> int:
+    """Natural auxiliary functions: B_out[:naux'] = U_kept^T B; returns naux'."""
+    k = ctypes.c_int32()
+    _check("dsrg_fno_naf", load().dsrg_fno_naf(int(nh), int(np_), int(naux), _ptr(B), float(threshold),
+                                              int(precision), _ptr(B_out), _ptr(w_out), ctypes.byref(k),
+                                              _stream(stream)))
+    return k.value
+
+
+def dsrg_fno_ladder(B_vv, T, C_out, precision=SLICED_BF16, stream=None):
+    """Particle-particle ladder C[p] = sum_cd <ab|cd> T[p][c][d] (device tensors)."""
+    naux, nv = int(B_vv.shape[0]), int(B_vv.shape[1])
+    _check("dsrg_fno_ladder", load().dsrg_fno_ladder(nv, naux, _ptr(B_vv), int(T.shape[0]), _ptr(T), int(precision),
+                                                    _ptr(C_out), _stream(stream)))
 
 
 def dsrg_fno_truncate_noalloc(nvir, dvv, mode, threshold, degen_ratio, on_out, no_out, stream=None) -> int:
@@ -361,3 +389,8 @@ def dsrg_fno_debug_pair_tiles(nslices, ncore, nact, nvir, pairs, energy_only=Fal
 def dsrg_fno_debug_set_barrier_limit(spins: int):
     """Spin limit of the eigensolver's grid barrier (<= 0: default)."""
     _check("dsrg_fno_debug_set_barrier_limit", load().dsrg_fno_debug_set_barrier_limit(int(spins)))
+
+
+def dsrg_fno_debug_set_fused_epilogue(on: bool):
+    """Eq. A7 epilogue inside the contraction kernel (True) or separate."""
+    _check("dsrg_fno_debug_set_fused_epilogue", load().dsrg_fno_debug_set_fused_epilogue(1 if on else 0))

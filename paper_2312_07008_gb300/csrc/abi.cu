@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "kernels.h"
@@ -140,8 +141,11 @@ static int validate(const dsrg_fno_problem* p) {
   if (p->nact > 16) return DSRG_FNO_ERR_UNSUPPORTED;
   if (p->ncore + p->nact == 0 || p->nvir == 0) return DSRG_FNO_ERR_ARG;
   if (!(p->s >= 0.0) || !isfinite(p->s)) return DSRG_FNO_ERR_ARG;
-  if (p->precision != DSRG_FNO_FP64 && p->precision != DSRG_FNO_SLICED_BF16) return DSRG_FNO_ERR_ARG;
+  if (p->precision < DSRG_FNO_FP64 || p->precision > DSRG_FNO_TF32) return DSRG_FNO_ERR_ARG;
   if (p->precision == DSRG_FNO_SLICED_BF16 && p->nslices != 0 && (p->nslices < 3 || p->nslices > 5))
+    return DSRG_FNO_ERR_UNSUPPORTED;
+  if (p->precision == DSRG_FNO_BF16X3 && p->nslices != 0 && p->nslices != 3) return DSRG_FNO_ERR_UNSUPPORTED;
+  if (p->precision == DSRG_FNO_TF32 && p->nslices != 0 && p->nslices != 1 && p->nslices != 3)
     return DSRG_FNO_ERR_UNSUPPORTED;
   if (p->naux > 0 && !is_device_ptr(p->B_hp)) return DSRG_FNO_ERR_ARG;
   if (!is_device_ptr(p->eps)) return DSRG_FNO_ERR_ARG;
@@ -187,12 +191,16 @@ struct PassBuffers {
   int nsplit;
   // fast form
   int ks;             // digit planes (0 = float64 form)
+  int2 pform;         // form and parts of the B.B contraction
   int kpad_q, kpad_v; // padded contraction lengths (naux, nvir)
   __nv_bfloat16 *planes_b, *planes_s;
   int *exps_b, *exps_s, *err;
   float2* nu;        // double-float contraction tiles
   float2* eps_dd;    // orbital energies as double-float
   unsigned* rowmax;  // max |hi| per row of the dressed matrices (float bits)
+  float2* hp;        // [nh np] eps_i - eps_a, double-float (fused epilogue)
+  const RegTables* reg;
+  bool fused;        // Eq. A7 epilogue inside the contraction kernel
   int2* tiles;       // output tiles of the pair contraction, all batches
   int* slot_of;      // [batch][nh][nh] slot of pair (i, j) in the batch, -1 outside
   std::vector<long> tile_begin;
@@ -205,9 +213,30 @@ static float2* as_dd(double* p) { return reinterpret_cast<float2*>(p); }
 
 static const int DEFAULT_SLICES = 5;
 
+// The Eq. A7 epilogue runs as its own kernel after the contraction (the
+// default: on GB300 the regulariser's 48 evaluations per thread at the end of
+// every tile, on the contraction kernel's four merge warps, stall the MMAs:
+// pair contraction 335 -> 554 ms per C2 solve, against 41 ms for the
+// separate kernel), or inside the contraction kernel's output stage.
+static std::atomic<int> g_fused_epilogue{0};
+bool fused_epilogue_enabled() { return g_fused_epilogue.load() != 0; }
+void set_fused_epilogue(bool on) { g_fused_epilogue.store(on ? 1 : 0); }
+
+// Digit planes of the fast-form stages (0 = float64 form).  The literal
+// forms of the precision study run every stage but the B.B contraction as
+// the default fast form.
 static int slices_of(const dsrg_fno_problem* p) {
-  if (p->precision != DSRG_FNO_SLICED_BF16) return 0;
+  if (p->precision == DSRG_FNO_FP64) return 0;
+  if (p->precision != DSRG_FNO_SLICED_BF16) return DEFAULT_SLICES;
   return p->nslices ? p->nslices : DEFAULT_SLICES;
+}
+
+// Form and parts of the B.B contraction: {FORM_DIGITS, ks}, {FORM_BF16X3, 2},
+// {FORM_TF32, 1 or 2}.
+static int2 pair_form_of(const dsrg_fno_problem* p, int ks) {
+  if (p->precision == DSRG_FNO_BF16X3) return make_int2(FORM_BF16X3, 2);
+  if (p->precision == DSRG_FNO_TF32) return make_int2(FORM_TF32, p->nslices == 1 ? 1 : 2);
+  return make_int2(FORM_DIGITS, ks);
 }
 
 static size_t doubles(size_t n) { return ws_bytes(n, sizeof(double)); }
@@ -260,15 +289,32 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
     // digit planes of B: rows (hole, particle), contraction over Q
     const long rows = (long)g.nh * g.np;
     DSRG_PHASE("phase_stage_b", st);
-    DSRG_TRY(slice_rows(W.ks, B, rows, g.nq, 1, rows, W.kpad_q, W.planes_b, W.exps_b, st));
+    if (W.pform.x == FORM_DIGITS)
+      DSRG_TRY(slice_rows(W.ks, B, rows, g.nq, 1, rows, W.kpad_q, W.planes_b, W.exps_b, st));
+    else
+      DSRG_TRY(stage_literal(W.pform.x, W.pform.y, B, rows, g.nq, 1, rows, W.kpad_q, W.planes_b, W.exps_b, st));
     DSRG_TRY(eps_to_dd(g.nh + g.nv, eps, W.eps_dd, st));
+    if (W.fused) DSRG_TRY(hole_particle_dd(g, eps, W.hp, st));
   }
   for (size_t bi = 0; bi < P.batches.size(); ++bi) {
     const Batch& b = P.batches[bi];
     double* ts = want_d ? W.ts : nullptr;
-    if (W.ks) {
-      DSRG_TRY(sliced_pair_gemm(W.ks, g, W.planes_b, W.exps_b, W.kpad_q, W.tiles + W.tile_begin[bi],
-                                W.tile_count[bi], W.slot_of + bi * (size_t)g.nh * g.nh, W.nu, W.err, st));
+    if (W.ks && W.fused) {
+      PairEpilogue epi{};
+      epi.hp = W.hp;
+      epi.reg = W.reg;
+      const float sh = (float)g.s;
+      epi.s_hi = sh;
+      epi.s_lo = (float)(g.s - (double)sh);
+      epi.tau = as_dd(W.tau);
+      epi.kap = as_dd(W.kap);
+      epi.ts = ts;
+      epi.nv = g.nv;
+      DSRG_TRY(sliced_pair_gemm(W.pform.y, W.pform.x, g, W.planes_b, W.exps_b, W.kpad_q, W.tiles + W.tile_begin[bi],
+                                W.tile_count[bi], W.slot_of + bi * (size_t)g.nh * g.nh, nullptr, &epi, W.err, st));
+    } else if (W.ks) {
+      DSRG_TRY(sliced_pair_gemm(W.pform.y, W.pform.x, g, W.planes_b, W.exps_b, W.kpad_q, W.tiles + W.tile_begin[bi],
+                                W.tile_count[bi], W.slot_of + bi * (size_t)g.nh * g.nh, W.nu, nullptr, W.err, st));
       DSRG_PHASE("phase_pair_epilogue", st);
       DSRG_TRY(pair_epilogue_dd(g, eps, W.eps_dd, W.pairs + b.pair_begin, b.npairs, W.nu, as_dd(W.tau),
                                 as_dd(W.kap), ts, st));
@@ -338,7 +384,7 @@ static int nsplit_for(int nv, int ndesc, int ks) {
 }
 
 // Carves the pass buffers out of the workspace (sizes must match pass_bytes).
-static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nsplit, int ks) {
+static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nsplit, int ks, int2 pform) {
   const size_t nv2 = (size_t)g.nv * g.nv;
   const int na = g.na, ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
   const int ntd = ceil_div(g.nv, 32);
@@ -361,17 +407,19 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
     b += ws_bytes((size_t)ks * rows * pad64(g.nq), 2) + ws_bytes(rows, sizeof(int));
     b += doubles((size_t)P.max_pairs * g.np * g.np);
     b += doubles((size_t)g.nh + g.nv);
+    b += doubles((size_t)g.nh * g.np);
     if (want_d)
       b += ws_bytes((size_t)ks * P.max_out * g.nv * pad64(g.nv), 2) + 2 * ws_bytes((size_t)P.max_out * g.nv, sizeof(int));
     b += ws_bytes(8, sizeof(int));
     size_t tiles = 0;
-    for (const Batch& bt : P.batches) tiles += (size_t)pair_tile_bound(ks, g, bt.npairs);
+    const int bn = pair_tile_n(pform.x, pform.y);
+    for (const Batch& bt : P.batches) tiles += (size_t)pair_tile_bound(bn, g, bt.npairs);
     b += ws_bytes(tiles + 1, sizeof(int2)) + ws_bytes(P.batches.size() * (size_t)g.nh * g.nh + 1, sizeof(int));
   }
   return b;
 }
 
-static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want_d, int nsplit, int ks,
+static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want_d, int nsplit, int ks, int2 pform,
                       PassBuffers& W, cudaStream_t st) {
   const size_t nv2 = (size_t)g.nv * g.nv;
   const int na = g.na, ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
@@ -400,6 +448,7 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
   W.nsplit = nsplit;
   if (!W.status) return DSRG_FNO_ERR_NOMEM;
   W.ks = ks;
+  W.pform = pform;
   if (ks) {
     const size_t rows = (size_t)g.nh * g.np;
     W.kpad_q = pad64(g.nq);
@@ -408,6 +457,9 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
     W.exps_b = ws_take<int>(ws, rows);
     W.nu = ws_take<float2>(ws, (size_t)P.max_pairs * g.np * g.np);
     W.eps_dd = ws_take<float2>(ws, (size_t)g.nh + g.nv);
+    W.hp = ws_take<float2>(ws, (size_t)g.nh * g.np);
+    W.fused = fused_epilogue_enabled();
+    if (W.fused) DSRG_TRY(reg_tables_device(&W.reg));
     if (want_d) {
       W.planes_s = ws_take<__nv_bfloat16>(ws, (size_t)ks * P.max_out * g.nv * W.kpad_v);
       W.exps_s = ws_take<int>(ws, (size_t)P.max_out * g.nv);
@@ -420,10 +472,11 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
     std::vector<int2> all, one;
     std::vector<int> slots(P.batches.size() * (size_t)g.nh * g.nh, -1);
     size_t bound = 0;
+    const int bn = pair_tile_n(pform.x, pform.y);
     for (size_t bi = 0; bi < P.batches.size(); ++bi) {
       const Batch& b = P.batches[bi];
-      bound += (size_t)pair_tile_bound(ks, g, b.npairs);
-      DSRG_TRY(pair_tiles(ks, g, P.pairs.data() + b.pair_begin, b.npairs, !want_d, one));
+      bound += (size_t)pair_tile_bound(bn, g, b.npairs);
+      DSRG_TRY(pair_tiles(bn, g, P.pairs.data() + b.pair_begin, b.npairs, !want_d, one));
       W.tile_begin.push_back((long)all.size());
       W.tile_count.push_back((int)one.size());
       all.insert(all.end(), one.begin(), one.end());
@@ -470,26 +523,26 @@ static int read_error_flag(const int* err, cudaStream_t st) {
 }
 
 // Energy-only pass for an arbitrary geometry (used for the MO and FNO bases).
-static int energy_pass(const Geometry& g, int ks, const double* B, const double* eps, const double* gamma1,
+static int energy_pass(const Geometry& g, int ks, int2 pform, const double* B, const double* eps, const double* gamma1,
                        const double* lambda2, Workspace& ws, size_t base_off, size_t budget, double* e_out,
                        cudaStream_t st) {
   Plan P;
   build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, budget), P);
   ws.off = base_off;
   PassBuffers W{};
-  size_t need = base_off + pass_bytes(g, P, false, 1, ks);
+  size_t need = base_off + pass_bytes(g, P, false, 1, ks, pform);
   if (need > ws.cap) return DSRG_FNO_ERR_NOMEM;
-  DSRG_TRY(carve_pass(ws, g, P, false, 1, ks, W, st));
+  DSRG_TRY(carve_pass(ws, g, P, false, 1, ks, pform, W, st));
   DSRG_TRY(run_pass(g, B, eps, gamma1, lambda2, P, W, false, nullptr, st));
   DSRG_CUDA(cudaMemcpyAsync(e_out, W.e_acc, sizeof(double), cudaMemcpyDeviceToHost, st));
   DSRG_CUDA(cudaStreamSynchronize(st));
   return read_error_flag(W.err, st);
 }
 
-static size_t energy_pass_bytes(const Geometry& g, int ks, size_t budget) {
+static size_t energy_pass_bytes(const Geometry& g, int ks, int2 pform, size_t budget) {
   Plan P;
   build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, budget), P);
-  return pass_bytes(g, P, false, 1, ks);
+  return pass_bytes(g, P, false, 1, ks, pform);
 }
 
 int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* e2_out, cudaStream_t st) {
@@ -498,10 +551,12 @@ int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
   if (!e2_out) return DSRG_FNO_ERR_ARG;
   const Geometry g = geometry_of(prob);
   const int ks = slices_of(prob);
-  DSRG_TRY(ws_reserve(ws, energy_pass_bytes(g, ks, budget) + ws_bytes(8, sizeof(int))));
+  const int2 pform = pair_form_of(prob, ks);
+  DSRG_TRY(ws_reserve(ws, energy_pass_bytes(g, ks, pform, budget) + ws_bytes(8, sizeof(int))));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
-  return energy_pass(g, ks, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, ws.off, budget, e2_out, st);
+  return energy_pass(g, ks, pform, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, ws.off, budget, e2_out,
+                     st);
 }
 
 int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
@@ -523,7 +578,8 @@ int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, dou
       small_fast ? ws_bytes(2 * (size_t)ks * g.nv * pad64(kmax), 2) + ws_bytes(2 * (size_t)g.nv, sizeof(int)) +
                        doubles((size_t)g.nv * g.nv) + ws_bytes(8, sizeof(int))
                  : 0;
-  size_t need = ws_bytes(8, sizeof(int)) + pass_bytes(g, P, true, nsplit, ks) + doubles((size_t)g.nh * g.nv) +
+  const int2 pform = pair_form_of(prob, ks);
+  size_t need = ws_bytes(8, sizeof(int)) + pass_bytes(g, P, true, nsplit, ks, pform) + doubles((size_t)g.nh * g.nv) +
                 doubles(small + 1) + small_fast_bytes;
   DSRG_TRY(ws_reserve(ws, need));
   int* flag = ws_take<int>(ws, 8);
@@ -537,7 +593,7 @@ int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, dou
     if (h) return DSRG_FNO_ERR_NONFINITE;
   }
   PassBuffers W{};
-  DSRG_TRY(carve_pass(ws, g, P, true, nsplit, ks, W, st));
+  DSRG_TRY(carve_pass(ws, g, P, true, nsplit, ks, pform, W, st));
   double* t1 = ws_take<double>(ws, (size_t)g.nh * g.nv);
   double* work = ws_take<double>(ws, small + 1);
   SmallFast sf{0, nullptr, nullptr, nullptr, nullptr};
@@ -615,8 +671,9 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
                  ws_bytes(nk + 8, sizeof(int)) + doubles((size_t)rows * gf.np + 1) + doubles(g.nh + nk + 1) +
                  doubles(nk + 1);
   const int ks = slices_of(prob);
-  size_t pass_mo = e2_mo_in ? 0 : energy_pass_bytes(g, ks, budget);
-  size_t pass_f = nk > 0 ? energy_pass_bytes(gf, ks, budget) : 0;
+  const int2 pform = pair_form_of(prob, ks);
+  size_t pass_mo = e2_mo_in ? 0 : energy_pass_bytes(g, ks, pform, budget);
+  size_t pass_f = nk > 0 ? energy_pass_bytes(gf, ks, pform, budget) : 0;
   const int kpv = pad64(nv);
   // B' = B U enters E_vv(FNO) element by element and Delta E is a difference
   // of two large energies: the rotation takes 6 digit planes (47 fraction
@@ -643,7 +700,8 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
   double e_mo = 0.0;
   if (e2_mo_in) e_mo = *e2_mo_in;
   else
-    DSRG_TRY(energy_pass(g, ks, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, base, budget, &e_mo, st));
+    DSRG_TRY(energy_pass(g, ks, pform, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, base, budget, &e_mo,
+                         st));
   double e_f = 0.0;
   if (nk > 0) {
     // F' = Vk^T diag(eps_v) Vk, recanonicalised: F' W = W eps'
@@ -681,7 +739,7 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
     DSRG_CUDA(cudaMemcpyAsync(epsf + g.nh, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
     if (eps_fno_out)
       DSRG_CUDA(cudaMemcpyAsync(eps_fno_out, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
-    DSRG_TRY(energy_pass(gf, ks, Bf, epsf, prob->gamma1, prob->lambda2, ws, base, budget, &e_f, st));
+    DSRG_TRY(energy_pass(gf, ks, pform, Bf, epsf, prob->gamma1, prob->lambda2, ws, base, budget, &e_f, st));
   }
   if (!isfinite(e_mo) || !isfinite(e_f)) return DSRG_FNO_ERR_NONFINITE;
   *de_out = e_mo - e_f;

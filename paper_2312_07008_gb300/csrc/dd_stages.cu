@@ -1,19 +1,10 @@
 // Elementwise stages of the fast form in double-float arithmetic:
 //   - the Eq. A7 regulariser applied to the contraction tiles (tau, kappa),
+//     regularizer.cuh,
 //   - the 2-RDM dressing of the vv classes with the energy partials.
 // Their float64 counterparts are gemm_f64.cu (fused epilogue) and dress.cu.
-//
-// Regulariser.  With x = s Delta^2 >= 0, y = exp(-x):
-//   tau = nu (1 - y) / Delta,  kappa = 2 nu - Delta tau = nu (1 + y).
-// exp(-x) follows the table method of Tang (ACM TOMS 15, 1989): t = x log2(e)
-// = n/64 + r with |r| <= 1/128, u = r ln 2, exp(-x) = 2^-q 2^-j/64 exp(-u),
-// n = 64 q + j, and exp(-u) from its Taylor series (to the cubic term in
-// double-float).  1 - y is formed without
-// cancellation: with C_j = 1 - 2^-j/64 and 1 - exp(-u) = u - u^2/2 + ...,
-//   1 - y = C_j + (1 - e^-u) - C_j (1 - e^-u)     (q = 0),
-// so that the small-Delta branch of Eq. A7 (R -> s Delta) keeps its relative
-// accuracy without a separate series.  For x > 40, y < 5e-18 is dropped.
 #include "dd.cuh"
+#include "regularizer.cuh"
 #include "dress_common.cuh"
 #include "kernels.h"
 
@@ -22,12 +13,6 @@ namespace dsrg {
 namespace {
 
 using namespace dressc;
-
-struct RegTables {
-  dd T[64];  // 2^-j/64
-  dd C[64];  // 1 - 2^-j/64
-  dd log2e, ln2, sixth;
-};
 
 // Filled once per device (float64 exp2 / expm1, then split); kernels copy it
 // to shared memory.
@@ -49,44 +34,6 @@ __device__ __forceinline__ void reg_tables_load(RegTables& R) {
   const float* src = reinterpret_cast<const float*>(&g_reg);
   float* dst = reinterpret_cast<float*>(&R);
   for (int k = threadIdx.x; k < (int)(sizeof(RegTables) / sizeof(float)); k += blockDim.x) dst[k] = src[k];
-}
-
-// R1 = (1 - exp(-s Delta^2)) / Delta and y = exp(-s Delta^2), double-float.
-__device__ __forceinline__ void regularize(dd delta, dd s, const RegTables& R, dd* r1, dd* y) {
-  if (delta.hi == 0.0f) {
-    *r1 = dd_make(0.0f);
-    *y = dd_make(1.0f);
-    return;
-  }
-  const dd x = dd_mul(s, dd_mul(delta, delta));
-  if (x.hi < 1e-20f) {  // R1 = s Delta (1 - x/2 + ...), y = 1 - x: the x terms are below the precision
-    *r1 = dd_mul(s, delta);
-    *y = dd_make(1.0f);
-    return;
-  }
-  if (x.hi > 40.0f) {
-    *y = dd_make(0.0f);
-    *r1 = dd_div(dd_make(1.0f), delta);
-    return;
-  }
-  const dd t = dd_mul(x, R.log2e);
-  const int n = __float2int_rn(t.hi * 64.0f);
-  const dd r = dd_sub(t, dd_make((float)n * 0.015625f));
-  const dd u = dd_mul(r, R.ln2);
-  const float uh = u.hi;
-  // 1 - e^-u = u - u^2/2 + u^3/6 - (u^4/24 - u^5/120 + u^6/720)   (|u| <= 0.0055)
-  // up to the cubic term in double-float; the rest (< 4e-11) in float
-  const dd u2 = dd_mul(u, u);
-  const dd c3 = dd_mul(dd_mul(u2, u), R.sixth);
-  const float tail = uh * uh * uh * uh * (1.0f / 24.0f - uh * (1.0f / 120.0f - uh * (1.0f / 720.0f)));
-  const dd omp = dd_add_f(dd_add_fast(dd_sub_fast(u, dd_mul_f(u2, 0.5f)), c3), -tail);
-  const dd p = dd_sub_fast(dd_make(1.0f), omp);
-  const int q = n >> 6, j = n & 63;
-  *y = dd_ldexp(dd_mul(R.T[j], p), -q);
-  dd omy;
-  if (q == 0) omy = dd_add_fast(R.C[j], dd_sub_fast(omp, dd_mul(R.C[j], omp)));
-  else omy = dd_sub_fast(dd_make(1.0f), *y);
-  *r1 = dd_div(omy, delta);
 }
 
 __global__ void eps_dd_kernel(int n, const double* __restrict__ eps, float2* __restrict__ out) {
@@ -335,6 +282,33 @@ static int ensure_reg_tables() {
     DSRG_CUDA(cudaStreamDestroy(s0));
     ready[dev] = true;
   }
+  return DSRG_FNO_OK;
+}
+
+// Device address of the current device's regulariser tables (filled first).
+int reg_tables_device(const RegTables** out) {
+  DSRG_TRY(ensure_reg_tables());
+  void* p = nullptr;
+  DSRG_CUDA(cudaGetSymbolAddress(&p, g_reg));
+  *out = static_cast<const RegTables*>(p);
+  return DSRG_FNO_OK;
+}
+
+__global__ void hole_particle_dd_kernel(Geometry g, const double* __restrict__ eps, float2* __restrict__ out) {
+  const long R = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= (long)g.nh * g.np) return;
+  const int i = (int)(R / g.np), a = (int)(R - (long)i * g.np);
+  const dd v = dd_from_double(eps[i] - eps[g.nc + a]);
+  out[R] = make_float2(v.hi, v.lo);
+}
+
+// hp[i np + a] = eps_i - eps_a (hole i, particle a) in double-float: the
+// denominator Delta^{ij}_{ab} = hp[i a] + hp[j b] of the fused epilogue.
+int hole_particle_dd(const Geometry& g, const double* eps, float2* out, cudaStream_t st) {
+  const long n = (long)g.nh * g.np;
+  if (n <= 0) return DSRG_FNO_OK;
+  hole_particle_dd_kernel<<<ceil_div(n, 256), 256, 0, st>>>(g, eps, out);
+  DSRG_LAUNCH_CHECK();
   return DSRG_FNO_OK;
 }
 

@@ -133,8 +133,9 @@ extern "C" int dsrg_fno_debug_pair_tiles(int32_t nslices, int32_t ncore, int32_t
     pr[k] = make_int2(pairs[2 * k], pairs[2 * k + 1]);
     if (pr[k].x < 0 || pr[k].y < pr[k].x || pr[k].y >= g.nh) return DSRG_FNO_ERR_ARG;
   }
-  DSRG_TRY(pair_tiles(nslices, g, pr.data(), npairs, energy_only != 0, out));
-  if ((long)out.size() > max_tiles || (long)out.size() > pair_tile_bound(nslices, g, npairs)) return DSRG_FNO_ERR_ARG;
+  const int bn = pair_tile_n(FORM_DIGITS, nslices);
+  DSRG_TRY(pair_tiles(bn, g, pr.data(), npairs, energy_only != 0, out));
+  if ((long)out.size() > max_tiles || (long)out.size() > pair_tile_bound(bn, g, npairs)) return DSRG_FNO_ERR_ARG;
   for (size_t t = 0; t < out.size(); ++t) {
     tiles[2 * t] = out[t].x;
     tiles[2 * t + 1] = out[t].y;
@@ -145,4 +146,49 @@ extern "C" int dsrg_fno_debug_pair_tiles(int32_t nslices, int32_t ncore, int32_t
 extern "C" int dsrg_fno_debug_set_barrier_limit(int64_t spins) {
   std::lock_guard<std::mutex> lk(workspace_mutex());
   return eig_set_barrier_limit((long long)spins);
+}
+
+extern "C" int dsrg_fno_debug_literal_gemm(int32_t precision, int32_t nterms, int32_t M, int32_t N, int32_t K,
+                                           const double* A, const double* B, double* C) {
+  int form, parts;
+  if (precision == DSRG_FNO_BF16X3 && (nterms == 0 || nterms == 3)) {
+    form = FORM_BF16X3;
+    parts = 2;
+  } else if (precision == DSRG_FNO_TF32 && (nterms == 0 || nterms == 1 || nterms == 3)) {
+    form = FORM_TF32;
+    parts = nterms == 1 ? 1 : 2;
+  } else {
+    return DSRG_FNO_ERR_ARG;
+  }
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return DSRG_FNO_ERR_ARG;
+  const int kp = pad64(K);
+  const int eb = form == FORM_TF32 ? 4 : 2;
+  DevBuf dA, dB, dC, pa, pb, ea, eb_, err;
+  DSRG_CUDA(cudaMalloc(&dA.p, sizeof(double) * M * K));
+  DSRG_CUDA(cudaMalloc(&dB.p, sizeof(double) * N * K));
+  DSRG_CUDA(cudaMalloc(&dC.p, sizeof(double) * M * N));
+  DSRG_CUDA(cudaMalloc(&pa.p, (size_t)eb * parts * M * kp));
+  DSRG_CUDA(cudaMalloc(&pb.p, (size_t)eb * parts * N * kp));
+  DSRG_CUDA(cudaMalloc(&ea.p, sizeof(int) * M));
+  DSRG_CUDA(cudaMalloc(&eb_.p, sizeof(int) * N));
+  DSRG_CUDA(cudaMalloc(&err.p, sizeof(int)));
+  DSRG_CUDA(cudaMemset(err.p, 0, sizeof(int)));
+  DSRG_CUDA(cudaMemcpy(dA.p, A, sizeof(double) * M * K, cudaMemcpyHostToDevice));
+  DSRG_CUDA(cudaMemcpy(dB.p, B, sizeof(double) * N * K, cudaMemcpyHostToDevice));
+  cudaStream_t st = 0;
+  DSRG_TRY(stage_literal(form, parts, (double*)dA.p, M, K, K, 1, kp, pa.p, (int*)ea.p, st));
+  DSRG_TRY(stage_literal(form, parts, (double*)dB.p, N, K, K, 1, kp, pb.p, (int*)eb_.p, st));
+  DSRG_TRY(sliced_plain_gemm(parts, M, N, pa.p, (int*)ea.p, pb.p, (int*)eb_.p, kp, (double*)dC.p, N, (int*)err.p, st,
+                             form));
+  int h = 0;
+  DSRG_CUDA(cudaMemcpy(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) return DSRG_FNO_ERR_TIMEOUT;
+  DSRG_CUDA(cudaMemcpy(C, dC.p, sizeof(double) * M * N, cudaMemcpyDeviceToHost));
+  return DSRG_FNO_OK;
+}
+
+extern "C" int dsrg_fno_debug_set_fused_epilogue(int32_t on) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  set_fused_epilogue(on != 0);
+  return DSRG_FNO_OK;
 }

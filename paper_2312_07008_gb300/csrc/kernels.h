@@ -115,12 +115,43 @@ int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int K
 // rowmax: NULL, or max |hi| per row as float bits (from dress_dd)
 int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
                   int* exps, const unsigned* rowmax, cudaStream_t st);
-int pair_tile_bound(int KS, const Geometry& g, int npairs);
-int pair_tiles(int KS, const Geometry& g, const int2* pairs, int npairs, bool energy_only, std::vector<int2>& out);
-int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
-                     const int2* tiles, int ntiles, const int* slot_of, float2* nu, int* err, cudaStream_t st);
+// Arithmetic forms of the contraction kernel: exact digit planes, or the
+// literal split-bf16 (3 terms) / tf32 (1 or 3 terms) products with float32
+// accumulation of the precision study.
+// FORM_DIGITS_T: the digit form with levels >= 3 accumulated per segment
+// (fewer merges; the dressed rank-K update, whose merges scale every
+// element by its segment's exponents, uses it).
+enum { FORM_DIGITS = 0, FORM_BF16X3 = 1, FORM_TF32 = 2, FORM_DIGITS_T = 3 };
+// N of the 128 x N output tiles of a form (KS: digit planes or literal parts)
+int pair_tile_n(int form, int KS);
+int pair_tile_bound(int BN, const Geometry& g, int npairs);
+int pair_tiles(int BN, const Geometry& g, const int2* pairs, int npairs, bool energy_only, std::vector<int2>& out);
+struct RegTables;
+// Eq. A7 epilogue fused into the pair contraction (see sliced.cu)
+struct PairEpilogue {
+  const float2* hp;       // [nh np] eps_i - eps_a, double-float
+  const RegTables* reg;   // regulariser tables of the device
+  float s_hi, s_lo;       // flow parameter s, double-float
+  float2* tau;            // [slot][nv][nv]
+  float2* kap;            // [slot][nv][nv]
+  double* ts;             // [nh][nh][nv][na] or null (energy only)
+  int nv;
+};
+// nu (double-float [slot][np][np]) of a batch, or with `epi` its tau, kappa
+// and ts directly (nu unused)
+int sliced_pair_gemm(int KS, int form, const Geometry& g, const void* planes, const int* exps, int Kpad,
+                     const int2* tiles, int ntiles, const int* slot_of, float2* nu, const PairEpilogue* epi, int* err,
+                     cudaStream_t st);
+// planes of a literal form: KS parts [KS][R][Kpad] (bf16 for FORM_BF16X3,
+// float32 holding tf32 values for FORM_TF32), exps[R] = 0
+int stage_literal(int form, int KS, const double* src, long R, int K, long rs, long ks, int Kpad, void* planes,
+                  int* exps, cudaStream_t st);
 // double-float elementwise stages (dd_stages.cu)
 int eps_to_dd(int n, const double* eps, float2* out, cudaStream_t st);
+int reg_tables_device(const RegTables** out);
+bool fused_epilogue_enabled();
+void set_fused_epilogue(bool on);
+int hole_particle_dd(const Geometry& g, const double* eps, float2* out, cudaStream_t st);
 int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd, const int2* pairs, int npairs,
                      const float2* nu, float2* tau, float2* kap, double* ts, cudaStream_t st);
 // rowmax: NULL, or [nout][nv] zeroed words receiving max |hi| of each row of
@@ -131,8 +162,8 @@ int dress_dd(const Geometry& g, const DressDesc* d_desc, int ndesc, int ncc, con
 int regularize_test(int n, const double* delta, double s, double* r1, double* y, cudaStream_t st);
 int sliced_syrk(int KS, int nv, int nr, const __nv_bfloat16* planes, const int* exps, int Kpad,
                 const double* sign, double* dpart, int nsplit, double* D, int* err, cudaStream_t st);
-int sliced_plain_gemm(int KS, int M, int N, const __nv_bfloat16* pa, const int* ea, const __nv_bfloat16* pb,
-                      const int* eb, int Kpad, double* C, long ldc, int* err, cudaStream_t st);
+int sliced_plain_gemm(int KS, int M, int N, const void* pa, const int* ea, const void* pb,
+                      const int* eb, int Kpad, double* C, long ldc, int* err, cudaStream_t st, int form = FORM_DIGITS);
 inline int pad64(int k) { return (k + 63) / 64 * 64; }
 
 // Truncation and correction helpers (fno.cu)

@@ -32,6 +32,7 @@
 
 #include "kernels.h"
 #include "mma_schedule.cuh"
+#include "regularizer.cuh"
 #include "tc_ptx.cuh"
 
 namespace dsrg {
@@ -191,6 +192,53 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const T* __restrict__ s
   }
 }
 
+// tf32 value of x (round to nearest, ties away from zero): 10 fraction bits
+// kept, the low 13 bits of the float32 container zero
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// Parts of a literal form: planes[s][row][k] (k padded with zeros to Kpad),
+// exps[row] = 0.  Source element (row, k) at src[row * rs + k * ks].
+template <int FORM, int KS>
+__global__ void __launch_bounds__(256) split_rows_kernel(const double* __restrict__ src, long R, int K, long rs,
+                                                         long ks, int Kpad, void* __restrict__ planes,
+                                                         int* __restrict__ exps) {
+  __shared__ double tile[32][33];
+  const long row0 = (long)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const bool kfast = (ks == 1);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = kfast ? ty + 8 * i : tx;
+    const int k = kfast ? tx : ty + 8 * i;
+    const long row = row0 + r;
+    tile[r][k] = (row < R && k0 + k < K) ? src[row * rs + (long)(k0 + k) * ks] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = ty + 8 * i;
+    const long row = row0 + r;
+    if (row >= R) continue;
+    const double v = tile[r][tx];
+    const long o = row * Kpad + k0 + tx;
+    if constexpr (FORM == FORM_BF16X3) {
+      __nv_bfloat16* pl = reinterpret_cast<__nv_bfloat16*>(planes);
+      const __nv_bfloat16 hi = __double2bfloat16(v);
+      pl[o] = hi;
+      pl[R * Kpad + o] = __double2bfloat16(v - (double)__bfloat162float(hi));
+    } else {
+      float* pl = reinterpret_cast<float*>(planes);
+      const float big = tf32_round((float)v);
+      pl[o] = big;
+      if (KS == 2) pl[R * Kpad + o] = tf32_round((float)(v - (double)big));
+    }
+  }
+  if (blockIdx.y == 0 && threadIdx.x < 32 && row0 + threadIdx.x < R) exps[row0 + threadIdx.x] = 0;
+}
+
 // exact 2^e in float32 (0 below the normal range)
 __device__ __forceinline__ float pow2f(int e) {
   if (e < -126) return 0.0f;
@@ -221,7 +269,12 @@ struct GemmParams {
   const int2* tiles;  // [njobs] (row tile, column tile)
   const int* slot_of; // [nh nh], -1 for a pair outside the batch
   int np, na, nh, rows;
-  float2* nu_out;   // [slot][np][np], double-float
+  float2* nu_out;   // [slot][np][np], double-float (when not fused)
+  // fused Eq. A7 epilogue (pair mode): tau and kappa of the vv elements
+  // (double-float, [slot][nv][nv]) and the semi-internal amplitudes
+  // ts[i][j][e][x] (float64) straight from the accumulators; nu is not stored
+  PairEpilogue epi;
+  int fused;
   // plain mode: C[m][n] = A[m] . B[n] (rows M x N), exps of A and B separately
   int M, N;
   const int* exps_b;
@@ -273,8 +326,19 @@ __device__ __forceinline__ void seg_range(const GemmParams& P, int split, int* r
   }
 }
 
-template <int KS, int BN, int STAGES>
+// Arithmetic forms of the kernel.  DIGITS: exact bf16 digit planes (above).
+// The literal forms, for the precision study of the B.B contraction: a value
+// is split into KS floating-point parts whose products the tensor core sums
+// into ONE float32 accumulator over the whole contraction (no chunk merges):
+//   BF16X3: x = hi + lo, hi = bf16(x), lo = bf16(x - hi); hi.hi + hi.lo + lo.hi
+//   TF32:   KS = 1: tf32(x) . tf32(y); KS = 2: big = tf32(x), small =
+//           tf32(x - big), big.big + big.small + small.big  (kind::tf32)
+template <int KS, int BN, int STAGES, int FORM>
 struct Cfg {
+  static constexpr bool DIG = FORM == FORM_DIGITS || FORM == FORM_DIGITS_T;  // digit planes
+  static constexpr int EB = FORM == FORM_TF32 ? 4 : 2;      // bytes per element
+  static constexpr int BKE_E = ROW_BYTES / EB;              // elements per 128-byte k block
+  static constexpr int NPROD = DIG ? KS * (KS + 1) / 2 : (KS == 1 ? 1 : 3);
   static constexpr int A_SLICE = BM * ROW_BYTES;
   static constexpr int B_SLICE = BN * ROW_BYTES;
   static_assert(A_SLICE % 1024 == 0 && B_SLICE % 1024 == 0, "plane tiles keep the 1024-byte swizzle atoms aligned");
@@ -288,19 +352,26 @@ struct Cfg {
   // every level is accumulated per chunk and merged after it (levels 0-2
   // exactly, see above), so one set of KS consecutive level accumulators,
   // double buffered, and each A plane needs one MMA per k step
-  static constexpr int NEXACT = KS;
+  static constexpr int NEXACT = FORM == FORM_DIGITS ? KS : (FORM == FORM_DIGITS_T ? (KS < 3 ? KS : 3) : 1);
   static constexpr int SET_COLS = NEXACT * BN;              // levels of one chunk
   static constexpr int TAIL_BASE = 2 * SET_COLS;             // lower levels of one segment
-  static constexpr int TAIL_COLS = (KS - NEXACT) * BN;
+  // levels accumulated per segment and merged once (none in the current
+  // configurations: the digit form merges every level per chunk, a literal
+  // form has a single accumulator)
+  static constexpr int TAIL_COLS = DIG ? (KS - NEXACT) * BN : 0;
   static_assert(2 * SET_COLS + 2 * (TAIL_COLS > 0 ? TAIL_COLS : 0) <= TMEM_COLS, "TMEM budget");
-  static_assert(stacked_n_valid(KS, BN, NEXACT), "stacked MMA widths");
+  static_assert(!DIG || stacked_n_valid(KS, BN, NEXACT), "stacked MMA widths");
+  static_assert(DIG || KS == 1 || KS == 2, "literal forms: one or two parts");
 };
 
-template <int KS, int BN, int STAGES>
+template <int KS, int BN, int STAGES, int FORM>
 __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                              const __grid_constant__ CUtensorMap mapB,
                                                              GemmParams P) {
-  using C = Cfg<KS, BN, STAGES>;
+  using C = Cfg<KS, BN, STAGES, FORM>;
+  // k blocks per chunk: the digit form merges exact level sums every 320 k;
+  // a literal form accumulates the whole contraction in float32
+  const int kchunk = C::DIG ? KCHUNK_BLOCKS : P.nkb;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE_BYTES);
@@ -367,8 +438,8 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             }
             uint8_t* sa = smem + s * C::STAGE_BYTES;
             tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-            tc::tma_load_3d(sa, &mapA, kb * BKE, arow, 0, &full[s]);
-            tc::tma_load_3d(sa + C::A_BYTES, &mapB, kb * BKE, brow, 0, &full[s]);
+            tc::tma_load_3d(sa, &mapA, kb * C::BKE_E, arow, 0, &full[s]);
+            tc::tma_load_3d(sa + C::A_BYTES, &mapB, kb * C::BKE_E, brow, 0, &full[s]);
           }
           if (*abort_flag) break;
         }
@@ -394,7 +465,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
         for (int r = r0; r < r1 && !*abort_flag; ++r) {
           // low-order levels of this segment accumulate in tail set `lt`
           const uint32_t lt = segc & 1;
-          if (KS > C::NEXACT) {
+          if (C::TAIL_COLS > 0) {
             if (!tc::mbar_wait(&lempty[lt], ((segc >> 1) & 1) ^ 1, WAIT_LIMIT)) {
               *abort_flag = 1;
               atomicExch(P.err, 5);
@@ -404,7 +475,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           }
           uint32_t set = 0;
           for (int kb = 0; kb < P.nkb; ++kb, ++it) {
-            const int kc = kb % KCHUNK_BLOCKS;
+            const int kc = kb % kchunk;
             if (kc == 0) {
               set = chunk & 1;
               if (!tc::mbar_wait(&tempty[set], ((chunk >> 1) & 1) ^ 1, WAIT_LIMIT)) {
@@ -431,6 +502,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             // consecutive levels m.level .. m.level + m.nb - 1, which lie one
             // after another in TMEM, and the B planes lie one after another in
             // shared memory: one MMA with N = m.nb BN does them all.
+            if constexpr (C::DIG) {
 #pragma unroll
             for (int i = 0; i < stacked_mma_count(KS, C::NEXACT); ++i) {
               const StackedMma m = stacked_mma(KS, i, C::NEXACT);
@@ -442,7 +514,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
               const bool first_block = exact ? (kc == 0) : (kb == 0);
               const uint32_t idesc = tc::make_idesc_bf16(BM, m.nb * BN);
 #pragma unroll
-              for (int kk = 0; kk < BKE / 16; ++kk) {
+              for (int kk = 0; kk < 4; ++kk) {  // 16 bf16 of k per MMA
                 // start-address field += byte offset / 16 (no carry: shared addresses < 2^18)
                 const uint64_t ad = a_desc0 + (uint64_t)((m.a * C::A_SLICE + kk * 32) >> 4);
                 const uint64_t bd = b_desc0 + (uint64_t)((m.b0 * C::B_SLICE + kk * 32) >> 4);
@@ -452,14 +524,30 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
                 tc::mma_bf16(d, ad, bd, idesc, acc);
               }
             }
+            } else {
+              // literal form: every product into one float32 accumulator
+              const uint32_t d = tmem + set * C::SET_COLS;
+#pragma unroll
+              for (int pi = 0; pi < C::NPROD; ++pi) {
+                const int pa = pi == 2 ? 1 : 0, pb = pi == 1 ? 1 : 0;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of k per MMA (16 bf16 or 8 tf32)
+                  const uint64_t ad = a_desc0 + (uint64_t)((pa * C::A_SLICE + kk * 32) >> 4);
+                  const uint64_t bd = b_desc0 + (uint64_t)((pb * C::B_SLICE + kk * 32) >> 4);
+                  const uint32_t acc = (kc == 0 && kk == 0 && pi == 0) ? 0u : 1u;
+                  if constexpr (FORM == FORM_TF32) tc::mma_tf32(d, ad, bd, tc::make_idesc_tf32(BM, BN), acc);
+                  else tc::mma_bf16(d, ad, bd, tc::make_idesc_bf16(BM, BN), acc);
+                }
+              }
+            }
             tc::mma_commit(&empty[s]);
-            if (kc == KCHUNK_BLOCKS - 1 || kb == P.nkb - 1) {
+            if (kc == kchunk - 1 || kb == P.nkb - 1) {
               tc::mma_commit(&tfull[set]);
               ++chunk;
             }
           }
           if (*abort_flag) break;
-          if (KS > C::NEXACT) tc::mma_commit(&lfull[lt]);
+          if (C::TAIL_COLS > 0) tc::mma_commit(&lfull[lt]);
           ++segc;
         }
       }
@@ -497,7 +585,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
         }
         // adds 2^(-14-8L) x level L (TMEM columns at col0) into the accumulators
         auto merge = [&](int L, uint32_t col0) {
-          const float lscale = pow2f(-14 - 8 * L) * rowscale;
+          const float lscale = (C::DIG ? pow2f(-14 - 8 * L) : 1.0f) * rowscale;
 #pragma unroll
           for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
@@ -513,7 +601,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
             }
           }
         };
-        const int nchunks = (P.nkb + KCHUNK_BLOCKS - 1) / KCHUNK_BLOCKS;
+        const int nchunks = (P.nkb + kchunk - 1) / kchunk;
         for (int c = 0; c < nchunks; ++c) {
           const uint32_t set = chunk & 1;
           if (!tc::mbar_wait(&tfull[set], (chunk >> 1) & 1, WAIT_LIMIT)) {
@@ -531,7 +619,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           ++chunk;
         }
         if (failed) break;
-        if (KS > C::NEXACT) {
+        if (C::TAIL_COLS > 0) {
           const uint32_t lt = segc & 1;
           if (!tc::mbar_wait(&lfull[lt], (segc >> 1) & 1, WAIT_LIMIT)) {
             *abort_flag = 1;
@@ -550,7 +638,56 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
       }
       if (failed) break;
       // ------------------------------------------------------ tile output
-      if (P.mode == MODE_PAIR) {
+      if (P.mode == MODE_PAIR && P.fused) {
+        const int R = mt * BM + row;
+        if (R < P.rows) {
+          const int i = R / P.np, a = R - i * P.np;
+          const int ea = P.exps[R];
+          const int* srow = P.slot_of + (long)i * P.nh;
+          const float2 hr = P.epi.hp[R];
+          const dd rowhp = {hr.x, hr.y}, sdd = {P.epi.s_hi, P.epi.s_lo};
+          const int nv = P.epi.nv, na = P.na;
+          const bool av = a >= na;
+          // the accumulators through local memory: one rolled loop over the
+          // columns keeps one copy of the regulariser's code
+          float2 nuv[BN];
+#pragma unroll
+          for (int c = 0; c < BN; ++c) nuv[c] = make_float2(hi[c], lo[c]);
+          int j = (nt * BN) / P.np, b = nt * BN - j * P.np;
+#pragma unroll 1
+          for (int c = 0; c < BN && j < P.nh; ++c) {
+            const int slot = srow[j];
+            const bool bv = b >= na;
+            // as the separate epilogue: vv -> tau, kappa; va -> ts[i][j];
+            // av -> ts[j][i] unless i == j (the va element of that pair writes it)
+            const bool want = slot >= 0 && (av || bv) && (av && bv ? true : (P.epi.ts != nullptr && (av || i != j)));
+            if (want) {
+              const int C = nt * BN + c;
+              const int sc = ea + P.exps[C];
+              const dd n = {ldexpf(nuv[c].x, sc), ldexpf(nuv[c].y, sc)};
+              const float2 hc = P.epi.hp[C];
+              const dd delta = dd_add(rowhp, dd{hc.x, hc.y});
+              dd r1, y;
+              regularize(delta, sdd, *P.epi.reg, &r1, &y);
+              const dd t = dd_mul(n, r1);
+              if (av && bv) {
+                const dd k = dd_mul(n, dd_add_f(y, 1.0f));
+                const long o = ((long)slot * nv + (a - na)) * nv + (b - na);
+                P.epi.tau[o] = make_float2(t.hi, t.lo);
+                P.epi.kap[o] = make_float2(k.hi, k.lo);
+              } else if (av) {
+                P.epi.ts[(((long)i * P.nh + j) * nv + (a - na)) * na + b] = dd_to_double(t);
+              } else {
+                P.epi.ts[(((long)j * P.nh + i) * nv + (b - na)) * na + a] = dd_to_double(t);
+              }
+            }
+            if (++b == P.np) {
+              b = 0;
+              ++j;
+            }
+          }
+        }
+      } else if (P.mode == MODE_PAIR) {
         const int R = mt * BM + row;
         if (R < P.rows) {
           const int i = R / P.np, a = R - i * P.np;
@@ -633,16 +770,17 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D map over planes [KS][rows][Kpad] bf16, box {BKE, box_rows, box_planes}, 128-byte swizzle.
+// 3-D map over planes [KS][rows][Kpad] (bf16, or float32 for tf32), box
+// {128 bytes of k, box_rows, box_planes}, 128-byte swizzle.
 int make_plane_map(CUtensorMap* map, const void* planes, int KS, long rows, int Kpad, int box_rows,
-                   int box_planes) {
+                   int box_planes, int eb) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return DSRG_FNO_ERR_CUDA;
   cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)KS};
-  cuuint64_t strides[2] = {(cuuint64_t)Kpad * 2, (cuuint64_t)rows * Kpad * 2};
-  cuuint32_t box[3] = {(cuuint32_t)BKE, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kpad * eb, (cuuint64_t)rows * Kpad * eb};
+  cuuint32_t box[3] = {(cuuint32_t)(ROW_BYTES / eb), (cuuint32_t)box_rows, (cuuint32_t)box_planes};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(planes), dims, strides, box, estr,
+  CUresult r = fn(map, eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(planes), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? DSRG_FNO_OK : DSRG_FNO_ERR_CUDA;
@@ -655,15 +793,17 @@ int num_sms() {
   return n > 0 ? n : 148;
 }
 
-template <int KS, int BN, int STAGES>
+template <int KS, int BN, int STAGES, int FORM = FORM_DIGITS>
 int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kpad, GemmParams P,
                 cudaStream_t st) {
-  using C = Cfg<KS, BN, STAGES>;
+  using C = Cfg<KS, BN, STAGES, FORM>;
   if (P.njobs <= 0) return DSRG_FNO_OK;
+  if (Kpad % C::BKE_E != 0) return DSRG_FNO_ERR_ARG;
+  P.nkb = Kpad / C::BKE_E;
   CUtensorMap ma, mb;
-  DSRG_TRY(make_plane_map(&ma, pa, KS, rows_a, Kpad, BM, KS));
-  DSRG_TRY(make_plane_map(&mb, pb, KS, rows_b, Kpad, BN, KS));
-  auto kern = sliced_gemm_kernel<KS, BN, STAGES>;
+  DSRG_TRY(make_plane_map(&ma, pa, KS, rows_a, Kpad, BM, KS, C::EB));
+  DSRG_TRY(make_plane_map(&mb, pb, KS, rows_b, Kpad, BN, KS, C::EB));
+  auto kern = sliced_gemm_kernel<KS, BN, STAGES, FORM>;
   // the same value on every launch (per device, idempotent, thread-safe)
   DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   const int grid = std::min(num_sms(), P.njobs);
@@ -678,7 +818,7 @@ int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kp
     } else {
       tiles = P.njobs;
     }
-    const double fl = 2.0 * BM * BN * (double)Kpad * (KS * (KS + 1) / 2) * (double)tiles;
+    const double fl = 2.0 * BM * BN * (double)Kpad * C::NPROD * (double)tiles;
     const char* nm = P.mode == MODE_PAIR ? "sliced_gemm_pair" : (P.mode == MODE_SYRK ? "sliced_gemm_syrk"
                                                                                       : "sliced_gemm_plain");
     prof_begin(nm, fl, st, &tok);
@@ -690,7 +830,19 @@ int launch_gemm(const void* pa, long rows_a, const void* pb, long rows_b, int Kp
 }
 
 int dispatch_gemm(int KS, const void* pa, long rows_a, const void* pb, long rows_b, int Kpad, GemmParams P,
-                  cudaStream_t st) {
+                  cudaStream_t st, int form = FORM_DIGITS) {
+  if (form == FORM_BF16X3) return launch_gemm<2, 64, 4, FORM_BF16X3>(pa, rows_a, pb, rows_b, Kpad, P, st);
+  if (form == FORM_TF32)
+    return KS == 1 ? launch_gemm<1, 64, 4, FORM_TF32>(pa, rows_a, pb, rows_b, Kpad, P, st)
+                   : launch_gemm<2, 64, 4, FORM_TF32>(pa, rows_a, pb, rows_b, Kpad, P, st);
+  if (P.mode == MODE_SYRK) {
+    switch (KS) {
+      case 3: return launch_gemm<3, 64, 3, FORM_DIGITS_T>(pa, rows_a, pb, rows_b, Kpad, P, st);
+      case 4: return launch_gemm<4, 64, 2, FORM_DIGITS_T>(pa, rows_a, pb, rows_b, Kpad, P, st);
+      case 5: return launch_gemm<5, 48, 2, FORM_DIGITS_T>(pa, rows_a, pb, rows_b, Kpad, P, st);
+      default: return DSRG_FNO_ERR_ARG;
+    }
+  }
   switch (KS) {
     case 3: return launch_gemm<3, 64, 3>(pa, rows_a, pb, rows_b, Kpad, P, st);
     case 4: return launch_gemm<4, 64, 2>(pa, rows_a, pb, rows_b, Kpad, P, st);
@@ -729,6 +881,19 @@ static int slice_rows_t(int KS, const T* src, long R, int K, long rs, long ks, i
   return DSRG_FNO_OK;
 }
 
+int stage_literal(int form, int KS, const double* src, long R, int K, long rs, long ks, int Kpad, void* planes,
+                  int* exps, cudaStream_t st) {
+  if (R <= 0) return DSRG_FNO_OK;
+  if (Kpad % 32 != 0) return DSRG_FNO_ERR_ARG;
+  dim3 grid((unsigned)((R + 31) / 32), (unsigned)(Kpad / 32));
+  if (form == FORM_BF16X3 && KS == 2) split_rows_kernel<FORM_BF16X3, 2><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps);
+  else if (form == FORM_TF32 && KS == 1) split_rows_kernel<FORM_TF32, 1><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps);
+  else if (form == FORM_TF32 && KS == 2) split_rows_kernel<FORM_TF32, 2><<<grid, 256, 0, st>>>(src, R, K, rs, ks, Kpad, planes, exps);
+  else return DSRG_FNO_ERR_ARG;
+  DSRG_LAUNCH_CHECK();
+  return DSRG_FNO_OK;
+}
+
 int slice_rows(int KS, const double* src, long R, int K, long rs, long ks, int Kpad, __nv_bfloat16* planes,
                int* exps, cudaStream_t st) {
   return slice_rows_t(KS, src, R, K, rs, ks, Kpad, planes, exps, nullptr, st);
@@ -749,15 +914,15 @@ int slice_rows_dd(int KS, const float2* src, long R, int K, long rs, long ks, in
 // one time share their A tiles (the band) and each B tile serves the band.
 static constexpr int ROW_BAND = 8;
 
-int pair_tile_bound(int KS, const Geometry& g, int npairs) {
-  const int BN = tile_n_for(KS);
+int pair_tile_n(int form, int KS) { return form == FORM_DIGITS ? tile_n_for(KS) : 64; }
+
+int pair_tile_bound(int BN, const Geometry& g, int npairs) {
   return npairs * (ceil_div(g.np, BM) + 1) * (ceil_div(g.np, BN) + 1);
 }
 
-int pair_tiles(int KS, const Geometry& g, const int2* pairs, int npairs, bool energy_only, std::vector<int2>& out) {
+int pair_tiles(int BN, const Geometry& g, const int2* pairs, int npairs, bool energy_only, std::vector<int2>& out) {
   out.clear();
   if (npairs <= 0) return DSRG_FNO_OK;
-  const int BN = tile_n_for(KS);
   const long np = g.np, na = g.na;
   const int lo = energy_only ? (int)na : 0;
   int mt0 = 1 << 30, mt1 = -1;
@@ -809,8 +974,9 @@ int pair_tiles(int KS, const Geometry& g, const int2* pairs, int npairs, bool en
 
 // nu[slot][a][b] of a batch of pairs from B planes ([KS][nh*np][Kpad]) over
 // the output tiles of pair_tiles (device copy) and the batch's slot table.
-int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, const int* exps, int Kpad,
-                     const int2* tiles, int ntiles, const int* slot_of, float2* nu, int* err, cudaStream_t st) {
+int sliced_pair_gemm(int KS, int form, const Geometry& g, const void* planes, const int* exps, int Kpad,
+                     const int2* tiles, int ntiles, const int* slot_of, float2* nu, const PairEpilogue* epi, int* err,
+                     cudaStream_t st) {
   GemmParams P{};
   P.mode = MODE_PAIR;
   P.nkb = Kpad / BKE;
@@ -823,9 +989,13 @@ int sliced_pair_gemm(int KS, const Geometry& g, const __nv_bfloat16* planes, con
   P.nh = g.nh;
   P.rows = g.nh * g.np;
   P.nu_out = nu;
+  if (epi) {
+    P.epi = *epi;
+    P.fused = 1;
+  }
   P.err = err;
   const long rows = (long)g.nh * g.np;
-  return dispatch_gemm(KS, planes, rows, planes, rows, Kpad, P, st);
+  return dispatch_gemm(KS, planes, rows, planes, rows, Kpad, P, st, form);
 }
 
 // D += sum_r sign_r Sig_r Sig_r^T from Sig planes ([KS][nr*nv][Kpad]).
@@ -856,13 +1026,13 @@ int sliced_syrk(int KS, int nv, int nr, const __nv_bfloat16* planes, const int* 
 }
 
 // C[m][n] (ldc) = A[m] . B[n] from planes of A ([KS][M][Kpad]) and B ([KS][N][Kpad]).
-int sliced_plain_gemm(int KS, int M, int N, const __nv_bfloat16* pa, const int* ea, const __nv_bfloat16* pb,
-                      const int* eb, int Kpad, double* C, long ldc, int* err, cudaStream_t st) {
+int sliced_plain_gemm(int KS, int M, int N, const void* pa, const int* ea, const void* pb,
+                      const int* eb, int Kpad, double* C, long ldc, int* err, cudaStream_t st, int form) {
   if (M <= 0 || N <= 0) return DSRG_FNO_OK;
   GemmParams P{};
   P.mode = MODE_PLAIN;
   P.nkb = Kpad / BKE;
-  const int BN = tile_n_for(KS);
+  const int BN = form == FORM_DIGITS ? tile_n_for(KS) : 64;
   P.ntm = ceil_div(M, BM);
   P.ntn = ceil_div(N, BN);
   P.njobs = P.ntm * P.ntn;
@@ -873,7 +1043,7 @@ int sliced_plain_gemm(int KS, int M, int N, const __nv_bfloat16* pa, const int* 
   P.c_out = C;
   P.ldc = ldc;
   P.err = err;
-  return dispatch_gemm(KS, pa, M, pb, N, Kpad, P, st);
+  return dispatch_gemm(KS, pa, M, pb, N, Kpad, P, st, form);
 }
 
 }  // namespace dsrg

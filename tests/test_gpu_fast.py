@@ -89,3 +89,32 @@ def test_fast_error_falls_with_digit_planes():
     print("E errors by planes 3/4/5:", e)
     assert e[5] < e[3] / 1000
     assert e[5] <= E_TOL
+
+
+@pytest.mark.parametrize("shape", [
+    dict(ncore=4, nact=3, nvir=150, naux=300, nstates=2),
+    dict(ncore=6, nact=0, nvir=97, naux=250, nstates=1),
+])
+def test_fused_epilogue_equals_the_separate_kernel(shape):
+    """The Eq. A7 regulariser in the contraction kernel's output stage gives
+    what the separate epilogue kernel gives from the stored contraction
+    tiles (the two form Delta with different double-float roundings: equal
+    to about 1e-13 relative), and both match the oracle."""
+    p = make_problem(seed=47, s=0.5, **shape)
+    ref = O.solve(p, cuts=(98.5,))
+    gp = pkg.problem_from_synth(p, "cuda", pkg.SLICED_BF16, 5)
+    nv = p.nvir
+    out = {}
+    try:
+        for fused in (False, True):
+            pkg.dsrg_fno_debug_set_fused_epilogue(fused)
+            d = torch.empty((nv, nv), dtype=torch.float64, device="cuda")
+            e2 = pkg.dsrg_fno_vv_opdm(gp, d)
+            out[fused] = (e2, d.cpu().numpy(), pkg.dsrg_fno_pt2_energy(gp))
+    finally:
+        pkg.dsrg_fno_debug_set_fused_epilogue(False)
+    (e0, d0, ee0), (e1, d1, ee1) = out[False], out[True]
+    assert abs(e1 - e0) <= 1e-12 * abs(e0) and abs(ee1 - ee0) <= 1e-12 * abs(e0)
+    assert np.max(np.abs(d1 - d0)) <= 1e-12 * np.max(np.abs(d0))
+    assert abs(e1 - ref["e2"]) <= E_TOL
+    assert np.max(np.abs(d1 - ref["dvv"])) <= 1e-9 * np.max(np.abs(ref["dvv"]))

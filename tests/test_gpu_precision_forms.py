@@ -1,0 +1,148 @@
+"""The precision study: the literal forms of the B.B contraction.
+
+BF16X3 (x = hi + lo in bfloat16, hi.hi + hi.lo + lo.hi) and TF32 (one tf32
+product, or big.big + big.small + small.big of a two-part tf32 split) run on
+the tensor cores with one float32 accumulator over the whole contraction.
+Kernel level: the product equals the float64 sum of the split parts'
+products up to float32 accumulation (the parts are formed here on the host
+from their definitions).  Pipeline level: every energy, ON and kept-orbital
+count of the stored-oracle workloads is compared with the oracle in every
+form (float64, digit planes k = 3, 4, 5, and the literal forms); the errors
+are printed, and with DSRG_PRECISION_OUT set written as JSON to that path.
+"""
+import ctypes
+import functools
+import glob
+import json
+import os
+
+import numpy as np
+import pytest
+
+from synth import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2312_07008_gb300 as pkg  # noqa: E402
+
+dp = ctypes.POINTER(ctypes.c_double)
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def round_sig(x, bits):
+    """x rounded to `bits` significant bits, ties to even (bfloat16: 8)."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.round(m * 2.0 ** bits) / 2.0 ** bits, e)
+
+
+def tf32(x32):
+    """float32 -> tf32 (10 fraction bits), ties away from zero."""
+    u = np.asarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = ((u + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return u.view(np.float32).astype(np.float64)
+
+
+def parts(form, terms, X):
+    if form == pkg.BF16X3:
+        hi = round_sig(X, 8)
+        return [hi, round_sig(X - hi, 8)]
+    big = tf32(X.astype(np.float32))
+    if terms == 1:
+        return [big]
+    return [big, tf32((X - big).astype(np.float32))]
+
+
+def literal_gemm(form, terms, A, B):
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.zeros((M, N))
+    st = pkg.load().dsrg_fno_debug_literal_gemm(form, terms, M, N, K, np.ascontiguousarray(A).ctypes.data_as(dp),
+                                                np.ascontiguousarray(B).ctypes.data_as(dp), C.ctypes.data_as(dp))
+    assert st == 0, st
+    return C
+
+
+@pytest.mark.parametrize("form,terms", [(pkg.BF16X3, 3), (pkg.TF32, 1), (pkg.TF32, 3)], ids=["bf16x3", "tf32", "tf32x3"])
+def test_literal_product_is_the_split_product_in_float32(form, terms):
+    rng = np.random.default_rng(7 + form + terms)
+    M, N, K = 260, 150, 1000
+    A = 0.05 * rng.standard_normal((M, K))
+    B = 0.05 * rng.standard_normal((N, K))
+    C = literal_gemm(form, terms, A, B)
+    pa, pb = parts(form, terms, A), parts(form, terms, B)
+    prods = [(0, 0)] if terms == 1 else [(0, 0), (0, 1), (1, 0)]
+    ref = sum(pa[i] @ pb[j].T for i, j in prods)
+    absum = sum(np.abs(pa[i]) @ np.abs(pb[j]).T for i, j in prods)
+    # float32 accumulation of 3K (or K) terms: at most n units of 2^-23 (truncating adds) of sum |a b|
+    n = K * len(prods)
+    assert np.all(np.abs(C - ref) <= n * 2.0 ** -23 * absum), np.max(np.abs(C - ref) / absum)
+    exact = A @ B.T
+    rel = np.max(np.abs(C - exact)) / np.max(np.abs(exact))
+    # the float32 accumulation error relative to sum |a b|: its mean shows a bias
+    acc = (C - ref) / absum
+    print(f"form {form} terms {terms}: max error vs float64 product / max |C| = {rel:.2e}; "
+          f"accumulation error / sum|ab|: mean {np.mean(acc):+.2e}, rms {np.sqrt(np.mean(acc ** 2)):.2e}")
+    # the split itself: bf16x3 drops lo.lo (~2^-16 relative), tf32 ~2^-11, tf32x3 ~2^-22
+    assert rel < {(pkg.BF16X3, 3): 1e-3, (pkg.TF32, 1): 3e-2, (pkg.TF32, 3): 1e-4}[(form, terms)]
+
+
+FILES = sorted(glob.glob(os.path.join(HERE, "golden", "*.json")))
+SINGLE = [f for f in FILES if "batch" not in os.path.basename(f)]
+FORMS = [("fp64", pkg.FP64, 0), ("digits k=3", pkg.SLICED_BF16, 3), ("digits k=4", pkg.SLICED_BF16, 4),
+         ("digits k=5", pkg.SLICED_BF16, 5), ("bf16x3", pkg.BF16X3, 0), ("tf32", pkg.TF32, 1),
+         ("tf32x3", pkg.TF32, 3)]
+
+
+@functools.lru_cache(maxsize=None)
+def problem(name):
+    return workload(name)
+
+
+def solve(p, cuts, precision, nslices):
+    gp = pkg.problem_from_synth(p, "cuda", precision, nslices)
+    nv = p.nvir
+    d = torch.empty((nv, nv), dtype=torch.float64, device="cuda")
+    e2 = pkg.dsrg_fno_vv_opdm(gp, d)
+    on = torch.empty(nv, dtype=torch.float64, device="cuda")
+    no = torch.empty((nv, nv), dtype=torch.float64, device="cuda")
+    out = {"e2": e2, "cuts": {}}
+    for i, c in enumerate(cuts):
+        k = (pkg.dsrg_fno_truncate(nv, d, pkg.MODE_PO, c, 0.01, on, no) if i == 0
+             else pkg.dsrg_fno_cut(nv, on, pkg.MODE_PO, c, 0.01))
+        de, _ = pkg.dsrg_fno_discarded_correction(gp, k, no, e2_mo=e2)
+        out["cuts"][c] = (k, de)
+    out["ons"] = on.cpu().numpy()
+    return out
+
+
+@pytest.mark.parametrize("path", SINGLE, ids=[os.path.basename(f)[:-5] for f in SINGLE])
+def test_precision_study_against_stored_oracle(path):
+    ref = json.load(open(path))
+    p = problem(ref["workload"])
+    cuts = [float(c) for c in ref["cuts"]]
+    ons_ref = np.array(ref["ons"])
+    rows = []
+    for label, prec, ns in FORMS:
+        got = solve(p, cuts, prec, ns)
+        row = {"workload": ref["workload"], "form": label, "dE": got["e2"] - ref["e2"],
+               "max_dON": float(np.max(np.abs(got["ons"] - ons_ref))),
+               "cuts": {str(c): {"nkept": got["cuts"][c][0], "nkept_oracle": ref["cuts"][str(c)]["nkept"],
+                                 "ddE": got["cuts"][c][1] - ref["cuts"][str(c)]["de"]} for c in cuts}}
+        rows.append(row)
+        assert np.isfinite(row["dE"]) and np.isfinite(row["max_dON"])
+        # every form stays within a relative 1e-3 of the oracle's energy
+        assert abs(row["dE"]) <= 1e-3 * abs(ref["e2"])
+        if label in ("fp64", "digits k=5"):
+            tol_e, tol_on = (1e-8, 1e-9) if label == "fp64" else (1e-7, 1e-8)
+            assert abs(row["dE"]) <= tol_e and row["max_dON"] <= tol_on
+            assert all(v["nkept"] == v["nkept_oracle"] for v in row["cuts"].values())
+    for r in rows:
+        cs = "; ".join(f"p_o {c}: N' {v['nkept']}/{v['nkept_oracle']} ddE {v['ddE']:+.2e}" for c, v in r["cuts"].items())
+        print(f"{r['workload']:40s} {r['form']:11s} dE {r['dE']:+.3e}  max|dON| {r['max_dON']:.2e}  {cs}")
+    out = os.environ.get("DSRG_PRECISION_OUT")
+    if out:
+        prev = json.load(open(out)) if os.path.exists(out) else []
+        json.dump(prev + rows, open(out, "w"), indent=1)
