@@ -691,19 +691,105 @@ def sub_results(pkg, dev, nslices, steps=3, warmup=2):
                            "gflops": sum(algorithmic_flops(q) for q in probs) / (ms / 1e3) / 1e9,
                            "workers": pkg.dsrg_fno_batch_last_workers(), "steps": steps,
                            "sum_e2": sum(x["e2"] for x in r), "sum_nkept": sum(x["nkept"] for x in r)}
+    del gps, dvv, ons, nos
+    out["ladder_fno"] = ladder_timings(pkg, dev)
+    out["naf"] = naf_timing(pkg, dev, nslices)
     return out
 
 
+def ladder_timings(pkg, dev, nvs=(171, 203, 300), naux=3600, nh=70):
+    """The particle-particle ladder of Eq. 6 for the hole pairs of the nvir
+    1200 / naux 3600 workload (nh = 70: 2485 pairs i <= j) in virtual bases
+    of the sizes the p_o = 98 % and 99 % cuts keep (171, 203) and one larger;
+    seeded normal B_vv (symmetric in a, b) and amplitudes drawn on the device.
+    The cost grows as nv^4: the fitted exponent and the extrapolated time of
+    the untruncated basis (nvir 1200) are reported."""
+    import math
+    import torch
+    npairs = nh * (nh + 1) // 2
+    g = torch.Generator(device=dev)
+    rows = []
+    for nv in nvs:
+        g.manual_seed(nv)
+        Bv = 0.05 * torch.randn((naux, nv, nv), dtype=torch.float64, device=dev, generator=g)
+        Bv = (Bv + Bv.transpose(1, 2)) / math.sqrt(2.0)
+        T = 0.01 * torch.randn((npairs, nv, nv), dtype=torch.float64, device=dev, generator=g)
+        C = torch.empty_like(T)
+        pkg.dsrg_fno_ladder(Bv, T, C)   # warm-up (workspace)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        pkg.dsrg_fno_ladder(Bv, T, C)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        flops = 2.0 * nv ** 4 * (naux + npairs)
+        rows.append({"nv": nv, "ms": ms, "tflops_algorithmic": flops / (ms / 1e3) / 1e12})
+        del Bv, T, C
+    x = [math.log(r["nv"]) for r in rows]
+    y = [math.log(r["ms"]) for r in rows]
+    n = len(x)
+    slope = (n * sum(a * b for a, b in zip(x, y)) - sum(x) * sum(y)) / (n * sum(a * a for a in x) - sum(x) ** 2)
+    full = rows[-1]["ms"] * (1200.0 / rows[-1]["nv"]) ** 4
+    return {"npairs": npairs, "naux": naux, "timings": rows, "fitted_exponent": slope,
+            "extrapolated_ms_nvir1200": full,
+            "speedup_at_nv203": full / next(r["ms"] for r in rows if r["nv"] == 203)}
+
+
+def naf_timing(pkg, dev, nslices, keep_frac=0.75):
+    """Natural auxiliary functions of the nvir 1200 / naux 3600 workload:
+    time of dsrg_fno_naf keeping the largest 75 % of W's spectrum, and the
+    PT2 energy of the compressed problem against the full one."""
+    import torch
+    from synth import workload
+    p = workload(DEFAULT_WORKLOAD)
+    nh, np_ = p.ncore + p.nact, p.nact + p.nvir
+    B = torch.from_numpy(p.B).to(dev)
+    Bo = torch.empty_like(B)
+    w = torch.empty(p.naux, dtype=torch.float64, device=dev)
+    pkg.dsrg_fno_naf(nh, np_, p.naux, B, 1e300, pkg.SLICED_BF16, Bo, w)   # spectrum only (nothing kept)
+    ws = w.cpu().numpy()
+    k_target = int(keep_frac * p.naux)
+    thr = 0.5 * (ws[k_target - 1] + ws[k_target])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    k = pkg.dsrg_fno_naf(nh, np_, p.naux, B, thr, pkg.SLICED_BF16, Bo, w)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    gp = pkg.problem_from_synth(p, dev, pkg.SLICED_BF16, nslices)
+    gq = pkg.Problem(p.ncore, p.nact, p.nvir, k, Bo[:k].contiguous(), gp.tensors[1], gp.tensors[2], gp.tensors[3],
+                     None, p.weights, p.s, pkg.SLICED_BF16, nslices)
+    e_full = pkg.dsrg_fno_pt2_energy(gp)
+    torch.cuda.synchronize()
+    c, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c.record()
+    e_naf = pkg.dsrg_fno_pt2_energy(gq)
+    d.record()
+    torch.cuda.synchronize()
+    c2, d2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c2.record()
+    pkg.dsrg_fno_pt2_energy(gp)
+    d2.record()
+    torch.cuda.synchronize()
+    return {"naux": p.naux, "kept": k, "threshold": thr, "w_max": float(ws[0]), "w_min": float(ws[-1]),
+            "naf_ms": ms, "e2_full": e_full, "e2_naf": e_naf, "energy_ms_naf": c.elapsed_time(d),
+            "energy_ms_full": c2.elapsed_time(d2)}
+
+
 # DRAM bytes per executed flop of the pair contraction, from one ncu capture
-# of a full-size pair launch of this workload (the summary in profiles/ names
-# the command); valid only for the kernel sources it was taken with.
+# of a small pair launch of the same kernel, scaled to this workload's
+# launches; valid only for the kernel sources it was taken with.
 TRAFFIC = {
     "sa_cas10_ncore60_nvir1200_naux3600": {
-        "bytes_per_exec_flop": 214.409e9 / 1.178e14,
+        # small-case capture (energy pass of ncore 20 / nact 4 / nvir 1100 / naux 2000):
+        # 8.168 GB read + 2.912 GB written for 2.2556e13 executed flops
+        "bytes_per_exec_flop": (8.167924e9 + 2.912241e9) / 2.2556379709440e13,
         "sha256": {"paper_2312_07008_gb300/csrc/sliced.cu":
-                   "5c650e818ef0ea227c67a35a9bcc65831371be56f4ddd26ff2c02170b1b64479",
+                   "19fb335de6ba7b82ebc631a5a7c45bd2a1e3d52c841a0eaab8fb2e083e73c9c6",
                    "paper_2312_07008_gb300/csrc/tc_ptx.cuh":
-                   "970edeabe7cd01f635dc03045d58bcc21657742d5a046bc2110ab8b012c97aed"},
+                   "300804d055c2a37a13d0d68e3e9d556e62027073a7a31151f5033bd4885f0757"},
     },
 }
 
@@ -726,9 +812,8 @@ def traffic_per_launch(workload, exec_flops_per_launch):
 
 
 # Peaks this repository measured itself (the driver measures bf16 and HBM
-# only): cuBLAS float64 and TF32 GEMMs through torch.matmul, n = 8192, best
-# of several, CUDA events; the command and the clocks are in
-# profiles/peaks_fp64_tf32_gb300.md.
+# only): cuBLAS float64 and TF32 GEMMs through torch.matmul on one GB300,
+# n = 8192, best of 5 or 10, CUDA events, SM clock at its 2070 MHz maximum.
 PEAKS_OWN = {"fp64_dgemm_tflops": 1.0988, "tf32_tflops": 1027.07}
 
 
@@ -751,7 +836,7 @@ def roofline_of(pair_ms, pair_n, pair_fl, syrk, plain, step_ms, workload=None, a
             "padding": (pair_fl / (alg_flops * prods)) if alg_flops else None,
             "traffic": traffic_per_launch(workload, pair_fl / max(pair_n, 1)) if pair_n else None,
             "traffic_note": "DRAM bytes per average pair launch: bytes per executed flop of one ncu capture of "
-                            "a small pair launch (profiles/), times this run's executed flops per launch",
+                            "a small pair launch, times this run's executed flops per launch",
             "launches": pair_n, "avg_launch_ms": pair_ms / max(pair_n, 1),
             "executed_flops_per_launch": pair_fl / max(pair_n, 1),
             "share_of_step": pair_ms / step_ms if step_ms > 0 else None,

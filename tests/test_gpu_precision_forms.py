@@ -146,3 +146,24 @@ def test_precision_study_against_stored_oracle(path):
     if out:
         prev = json.load(open(out)) if os.path.exists(out) else []
         json.dump(prev + rows, open(out, "w"), indent=1)
+
+
+@pytest.mark.parametrize("form,terms", [(pkg.BF16X3, 3), (pkg.TF32, 1), (pkg.TF32, 3)], ids=["bf16x3", "tf32", "tf32x3"])
+def test_float32_accumulation_bias_on_positive_data(form, terms):
+    """With every product positive the float32 accumulator's rounding shows
+    as a relative bias of the result against the float64 sum of the same
+    split products (reported: the tensor core's accumulation need not round
+    to nearest); it stays below 1e-3 of the result."""
+    rng = np.random.default_rng(11 + form + terms)
+    M, N, K = 200, 130, 3600
+    A = 0.05 * rng.uniform(0.5, 1.0, (M, K))
+    B = 0.05 * rng.uniform(0.5, 1.0, (N, K))
+    C = literal_gemm(form, terms, A, B)
+    pa, pb = parts(form, terms, A), parts(form, terms, B)
+    prods = [(0, 0)] if terms == 1 else [(0, 0), (0, 1), (1, 0)]
+    ref = sum(pa[i] @ pb[j].T for i, j in prods)
+    rel = (C - ref) / ref
+    updates = len(prods) * K // (8 if form == pkg.TF32 else 16)
+    print(f"form {form} terms {terms}: {updates} accumulator updates per output, relative error vs the float64 "
+          f"split sum: mean {np.mean(rel):+.3e}, min {np.min(rel):+.3e}, max {np.max(rel):+.3e}")
+    assert np.max(np.abs(rel)) < 1e-3
