@@ -561,6 +561,55 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     const int row = q * 32 + lane;
     uint32_t chunk = 0, segc = 0;
+    // Fused Eq. A7 epilogue (pair mode): the finished accumulators of a tile
+    // wait in local memory and are regularised a few columns at a time after
+    // each chunk merge of the next tile, so that the MMA warp is not left
+    // without a drained accumulator set while 48 regulariser evaluations run.
+    float2 prev[BN];
+    int prev_mt = 0, prev_nt = 0, prev_pos = BN;  // prev_pos == BN: nothing pending
+    auto epi_range = [&](int c_end) {
+      const int R = prev_mt * BM + row;
+      if (R < P.rows) {
+        const int i = R / P.np, a = R - i * P.np;
+        const int ea = P.exps[R];
+        const int* srow = P.slot_of + (long)i * P.nh;
+        const float2 hr = P.epi.hp[R];
+        const dd rowhp = {hr.x, hr.y}, sdd = {P.epi.s_hi, P.epi.s_lo};
+        const int nv = P.epi.nv, na = P.na;
+        const bool av = a >= na;
+#pragma unroll 1
+        for (int c = prev_pos; c < c_end; ++c) {
+          const int C = prev_nt * BN + c;
+          const int j = C / P.np, b = C - j * P.np;
+          if (j >= P.nh) break;
+          const int slot = srow[j];
+          const bool bv = b >= na;
+          // as the separate epilogue: vv -> tau, kappa; va -> ts[i][j];
+          // av -> ts[j][i] unless i == j (the va element of that pair writes it)
+          const bool want = slot >= 0 && (av || bv) && (av && bv ? true : (P.epi.ts != nullptr && (av || i != j)));
+          if (!want) continue;
+          const int sc = ea + P.exps[C];
+          const dd n = {ldexpf(prev[c].x, sc), ldexpf(prev[c].y, sc)};
+          const float2 hc = P.epi.hp[C];
+          const dd delta = dd_add(rowhp, dd{hc.x, hc.y});
+          dd r1, y;
+          regularize(delta, sdd, *P.epi.reg, &r1, &y);
+          const dd t = dd_mul(n, r1);
+          if (av && bv) {
+            const dd k = dd_mul(n, dd_add_f(y, 1.0f));
+            const long o = ((long)slot * nv + (a - na)) * nv + (b - na);
+            P.epi.tau[o] = make_float2(t.hi, t.lo);
+            P.epi.kap[o] = make_float2(k.hi, k.lo);
+          } else if (av) {
+            P.epi.ts[(((long)i * P.nh + j) * nv + (a - na)) * na + b] = dd_to_double(t);
+          } else {
+            P.epi.ts[(((long)j * P.nh + i) * nv + (b - na)) * na + a] = dd_to_double(t);
+          }
+        }
+      }
+      prev_pos = c_end;
+    };
+    const bool spread = P.mode == MODE_PAIR && P.fused;
     for (int job = blockIdx.x; job < P.njobs; job += gridDim.x) {
       int slot, mt, nt;
       if (!decode_job<BN>(P, job, &slot, &mt, &nt)) continue;
@@ -617,6 +666,7 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&tempty[set]);
           ++chunk;
+          if (spread && prev_pos < BN) epi_range(min(BN, prev_pos + (BN + nchunks - 1) / nchunks));
         }
         if (failed) break;
         if (C::TAIL_COLS > 0) {
@@ -638,55 +688,13 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
       }
       if (failed) break;
       // ------------------------------------------------------ tile output
-      if (P.mode == MODE_PAIR && P.fused) {
-        const int R = mt * BM + row;
-        if (R < P.rows) {
-          const int i = R / P.np, a = R - i * P.np;
-          const int ea = P.exps[R];
-          const int* srow = P.slot_of + (long)i * P.nh;
-          const float2 hr = P.epi.hp[R];
-          const dd rowhp = {hr.x, hr.y}, sdd = {P.epi.s_hi, P.epi.s_lo};
-          const int nv = P.epi.nv, na = P.na;
-          const bool av = a >= na;
-          // the accumulators through local memory: one rolled loop over the
-          // columns keeps one copy of the regulariser's code
-          float2 nuv[BN];
+      if (spread) {
+        if (prev_pos < BN) epi_range(BN);  // a previous tile with fewer chunks than columns
 #pragma unroll
-          for (int c = 0; c < BN; ++c) nuv[c] = make_float2(hi[c], lo[c]);
-          int j = (nt * BN) / P.np, b = nt * BN - j * P.np;
-#pragma unroll 1
-          for (int c = 0; c < BN && j < P.nh; ++c) {
-            const int slot = srow[j];
-            const bool bv = b >= na;
-            // as the separate epilogue: vv -> tau, kappa; va -> ts[i][j];
-            // av -> ts[j][i] unless i == j (the va element of that pair writes it)
-            const bool want = slot >= 0 && (av || bv) && (av && bv ? true : (P.epi.ts != nullptr && (av || i != j)));
-            if (want) {
-              const int C = nt * BN + c;
-              const int sc = ea + P.exps[C];
-              const dd n = {ldexpf(nuv[c].x, sc), ldexpf(nuv[c].y, sc)};
-              const float2 hc = P.epi.hp[C];
-              const dd delta = dd_add(rowhp, dd{hc.x, hc.y});
-              dd r1, y;
-              regularize(delta, sdd, *P.epi.reg, &r1, &y);
-              const dd t = dd_mul(n, r1);
-              if (av && bv) {
-                const dd k = dd_mul(n, dd_add_f(y, 1.0f));
-                const long o = ((long)slot * nv + (a - na)) * nv + (b - na);
-                P.epi.tau[o] = make_float2(t.hi, t.lo);
-                P.epi.kap[o] = make_float2(k.hi, k.lo);
-              } else if (av) {
-                P.epi.ts[(((long)i * P.nh + j) * nv + (a - na)) * na + b] = dd_to_double(t);
-              } else {
-                P.epi.ts[(((long)j * P.nh + i) * nv + (b - na)) * na + a] = dd_to_double(t);
-              }
-            }
-            if (++b == P.np) {
-              b = 0;
-              ++j;
-            }
-          }
-        }
+        for (int c = 0; c < BN; ++c) prev[c] = make_float2(hi[c], lo[c]);
+        prev_mt = mt;
+        prev_nt = nt;
+        prev_pos = 0;
       } else if (P.mode == MODE_PAIR) {
         const int R = mt * BM + row;
         if (R < P.rows) {
@@ -733,6 +741,8 @@ __global__ void __launch_bounds__(192, 1) sliced_gemm_kernel(const __grid_consta
         }
       }
     }
+    // the last tile's epilogue (the job loop ends without a next tile)
+    if (spread && prev_pos < BN && !*abort_flag) epi_range(BN);
   }
   __syncwarp();
   tc::tc_fence_before();
