@@ -73,6 +73,17 @@ int dsrg_fno_debug_set_barrier_limit(int64_t spins);
  * this process. */
 int dsrg_fno_debug_set_fused_epilogue(int32_t on);
 
+/* Digit planes of the dressed matrices in the fast form's rank-K update of
+ * D_vv: 0 (default) = 4 when the problem uses 5 planes, else the problem's
+ * count; 3..5 = that many (at most the problem's count).  Affects later
+ * calls of this process. */
+int dsrg_fno_debug_set_syrk_planes(int32_t nslices);
+
+/* on != 0 (the default): symmetric eigensolves above 80 x 80 run on the
+ * column-pair Jacobi kernel; 0: on the round-parallel kernel over A in
+ * global memory (for comparison).  Affects later calls of this process. */
+int dsrg_fno_debug_set_eig_colpair(int32_t on);
+
 /* Bytes of device workspace the single-instance calls hold on the current
  * device (grow-only; 0 before the first call and after dsrg_fno_release()).
  * Host only: reads the library's bookkeeping, launches nothing. */

@@ -40,6 +40,8 @@ EXPORTED = (
     "dsrg_fno_debug_pair_tiles",
     "dsrg_fno_debug_set_barrier_limit",
     "dsrg_fno_debug_set_fused_epilogue",
+    "dsrg_fno_debug_set_syrk_planes",
+    "dsrg_fno_debug_set_eig_colpair",
     "dsrg_fno_set_log_callback",
     "dsrg_fno_profile_enable",
     "dsrg_fno_profile_query",
@@ -128,6 +130,10 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_debug_pair_tiles.argtypes = [i32, i32, i32, i32, ctypes.POINTER(i32), i32, i32,
                                               ctypes.POINTER(i32), i32]
     lib.dsrg_fno_debug_pair_tiles.restype = ctypes.c_int
+    lib.dsrg_fno_debug_set_eig_colpair.argtypes = [i32]
+    lib.dsrg_fno_debug_set_eig_colpair.restype = ctypes.c_int
+    lib.dsrg_fno_debug_set_syrk_planes.argtypes = [i32]
+    lib.dsrg_fno_debug_set_syrk_planes.restype = ctypes.c_int
     lib.dsrg_fno_debug_set_fused_epilogue.argtypes = [i32]
     lib.dsrg_fno_debug_set_fused_epilogue.restype = ctypes.c_int
     lib.dsrg_fno_debug_set_barrier_limit.argtypes = [ctypes.c_int64]
@@ -394,3 +400,13 @@ def dsrg_fno_debug_set_barrier_limit(spins: int):
 def dsrg_fno_debug_set_fused_epilogue(on: bool):
     """Eq. A7 epilogue inside the contraction kernel (True) or separate."""
     _check("dsrg_fno_debug_set_fused_epilogue", load().dsrg_fno_debug_set_fused_epilogue(1 if on else 0))
+
+
+def dsrg_fno_debug_set_syrk_planes(nslices: int):
+    """Digit planes of the rank-K update of D_vv (0: library rule)."""
+    _check("dsrg_fno_debug_set_syrk_planes", load().dsrg_fno_debug_set_syrk_planes(int(nslices)))
+
+
+def dsrg_fno_debug_set_eig_colpair(on: bool):
+    """Column-pair Jacobi kernel (True, default) or the round-parallel one."""
+    _check("dsrg_fno_debug_set_eig_colpair", load().dsrg_fno_debug_set_eig_colpair(1 if on else 0))

@@ -191,6 +191,7 @@ struct PassBuffers {
   int nsplit;
   // fast form
   int ks;             // digit planes (0 = float64 form)
+  int ks_d;           // digit planes of the dressed matrices (rank-K update)
   int2 pform;         // form and parts of the B.B contraction
   int kpad_q, kpad_v; // padded contraction lengths (naux, nvir)
   __nv_bfloat16 *planes_b, *planes_s;
@@ -229,6 +230,20 @@ static int slices_of(const dsrg_fno_problem* p) {
   if (p->precision == DSRG_FNO_FP64) return 0;
   if (p->precision != DSRG_FNO_SLICED_BF16) return DEFAULT_SLICES;
   return p->nslices ? p->nslices : DEFAULT_SLICES;
+}
+
+// Digit planes of the dressed matrices in the rank-K update of D_vv.  They
+// enter D_vv only (never an energy): with 4 planes (31 fraction bits) the
+// first dropped level, biased on D's diagonal by its square term, is about
+// 2^-32 of D, 4e-10 of an occupation number of ~2, against the 1e-8
+// tolerance, for two thirds of the digit products of 5 planes.  A test hook
+// can set the count (0 = this rule).
+static std::atomic<int> g_syrk_planes{0};
+void set_syrk_planes(int k) { g_syrk_planes.store(k); }
+static int syrk_slices(int ks) {
+  const int f = g_syrk_planes.load();
+  if (f >= 3 && f <= 5) return std::min(f, ks);
+  return ks >= 5 ? 4 : ks;
 }
 
 // Form and parts of the B.B contraction: {FORM_DIGITS, ks}, {FORM_BF16X3, 2},
@@ -339,10 +354,10 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
         const long rows = (long)b.nout * g.nv;
         {
           DSRG_PHASE("phase_stage_sig", st);
-          DSRG_TRY(slice_rows_dd(W.ks, as_dd(W.sig), rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, W.rowmax,
+          DSRG_TRY(slice_rows_dd(W.ks_d, as_dd(W.sig), rows, g.nv, g.nv, 1, W.kpad_v, W.planes_s, W.exps_s, W.rowmax,
                                  st));
         }
-        DSRG_TRY(sliced_syrk(W.ks, g.nv, b.nout, W.planes_s, W.exps_s, W.kpad_v, W.sig_sign, W.dpart, W.nsplit, D,
+        DSRG_TRY(sliced_syrk(W.ks_d, g.nv, b.nout, W.planes_s, W.exps_s, W.kpad_v, W.sig_sign, W.dpart, W.nsplit, D,
                              W.err, st));
       } else {
         DSRG_TRY(syrk_dressed_f64(g.nv, b.nout, W.sig, W.sig_sign, W.dpart, W.nsplit, D, st));
@@ -448,6 +463,7 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
   W.nsplit = nsplit;
   if (!W.status) return DSRG_FNO_ERR_NOMEM;
   W.ks = ks;
+  W.ks_d = ks ? syrk_slices(ks) : 0;
   W.pform = pform;
   if (ks) {
     const size_t rows = (size_t)g.nh * g.np;
@@ -570,7 +586,7 @@ int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, dou
   const int ks = slices_of(prob);
   Plan P;
   build_plan(g.nc, g.na, pair_cap_for_budget(g.nv, g.np, ks, budget), P);
-  const int nsplit = nsplit_for(g.nv, P.max_out, ks);
+  const int nsplit = nsplit_for(g.nv, P.max_out, ks ? syrk_slices(ks) : 0);
   const size_t small = small_terms_work_doubles(g.nc, g.na, g.nv);
   const int kmax = small_terms_kmax(g.nc, g.na);
   const bool small_fast = ks > 0 && kmax >= SLICED_MIN_K;

@@ -192,3 +192,16 @@ extern "C" int dsrg_fno_debug_set_fused_epilogue(int32_t on) {
   set_fused_epilogue(on != 0);
   return DSRG_FNO_OK;
 }
+
+extern "C" int dsrg_fno_debug_set_syrk_planes(int32_t nslices) {
+  if (nslices != 0 && (nslices < 3 || nslices > 5)) return DSRG_FNO_ERR_ARG;
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  set_syrk_planes(nslices);
+  return DSRG_FNO_OK;
+}
+
+extern "C" int dsrg_fno_debug_set_eig_colpair(int32_t on) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  set_eig_colpair(on != 0);
+  return DSRG_FNO_OK;
+}

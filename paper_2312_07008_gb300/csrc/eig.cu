@@ -18,6 +18,8 @@
 // is not the exact annihilating angle, and the next sweep removes what is
 // left of a_pq.  A is double-buffered (every block of A' reads four entries
 // of A); V is updated in place (a thread owns a column pair).
+#include <atomic>
+
 #include "dd.cuh"
 #include "kernels.h"
 
@@ -60,26 +62,27 @@ struct JacobiArgs {
 
 // Grid barrier (all blocks are co-resident: cooperative launch).  Returns
 // false once any block's wait has expired; the kernel then returns.
-__device__ bool grid_barrier(const JacobiArgs& P) {
+// bar: [0] arrivals, [1] generation; status[1] is set when a wait expires.
+__device__ bool grid_barrier_at(unsigned* bar, int* status) {
   __syncthreads();
   if (gridDim.x == 1) return true;  // one block: the block barrier is the grid barrier
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = P.bar + 1;
-    volatile int* st = P.status + 1;
+    volatile unsigned* gen = bar + 1;
+    volatile int* st = status + 1;
     const unsigned g = *gen;
     __threadfence();
     int ok = *st == 0;
     const long long limit = g_bar_spin_limit;
-    if (atomicAdd(P.bar, 1u) == gridDim.x - 1) {
-      atomicExch(P.bar, 0u);
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
       __threadfence();
-      atomicAdd(P.bar + 1, 1u);
+      atomicAdd(bar + 1, 1u);
     } else {
       long long it = 0;
       while (ok && *gen == g) {
         if (++it > limit || *st != 0) {
-          atomicExch(P.status + 1, 1);
+          atomicExch(status + 1, 1);
           ok = 0;
         }
         __nanosleep(100);
@@ -91,6 +94,8 @@ __device__ bool grid_barrier(const JacobiArgs& P) {
   __syncthreads();
   return s_ok != 0;
 }
+
+__device__ bool grid_barrier(const JacobiArgs& P) { return grid_barrier_at(P.bar, P.status); }
 
 __device__ __forceinline__ dd ldd(const float2* p, int i) {
   const float2 v = __ldcg(p + i);
@@ -332,6 +337,253 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
 }
 
 
+// The rotation (c, s) that annihilates a_pq (a_pp, a_qq, a_pq double-float):
+// t from float32 arithmetic on the double-float difference, c and s in
+// double-float renormalised so that c^2 + s^2 = 1 to working precision.
+__device__ __forceinline__ float4 jacobi_rotation(dd app, dd aqq, dd apq) {
+  if (apq.hi == 0.0f) return make_float4(1.f, 0.f, 0.f, 0.f);
+  const dd d = dd_sub(aqq, app);
+  const float th = d.hi / (2.0f * apq.hi);
+  const float t = (th >= 0.0f ? 1.0f : -1.0f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));
+  dd c = dd_rsqrt12(dd_add_f(two_prod(t, t), 1.0f));
+  dd sn = dd_mul_f(c, t);
+  const float g = dd_sub(dd_add(dd_mul(c, c), dd_mul(sn, sn)), dd_make(1.0f)).hi;
+  c = dd_add(c, dd_mul_f(c, -0.5f * g));
+  sn = dd_add(sn, dd_mul_f(sn, -0.5f * g));
+  return make_float4(c.hi, c.lo, sn.hi, sn.lo);
+}
+
+// position of index j in round r of the round-robin ordering (inverse of rr_index)
+__device__ __forceinline__ int rr_position(int j, int r, int m) {
+  return j == 0 ? 0 : ((j - 1 - r) % (m - 1) + (m - 1)) % (m - 1) + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Column-pair Jacobi.  The same cyclic two-sided Jacobi with round-robin
+// pairs, organised around column pairs: in a round, block b owns the column
+// pairs k in [b cp, (b+1) cp) of A and V.  For its pair (p, q) it reads
+// columns p and q (A in column-major double-float; A stays symmetric), forms
+// M = A J on them, then A' = J^T M for every row pair of the round (the
+// rotations of all pairs are known to every block), rotates V's columns p, q,
+// and writes the columns back.  With the new columns it publishes a_jj and
+// a_{partner(j), j} for the next round's pairing, from which every block
+// forms all rotations of the next round: one grid barrier per round, the
+// matrix moving through L2 once per round.
+struct ColPairArgs {
+  int n, m, half, cp;
+  const double* A_in;
+  double* A_out;
+  double* V_out;
+  float2* Ac;    // [n][n]: Ac[j][i] = A[i][j]
+  float2* Vc;    // [n][n]: Vc[j][i] = V[i][j]
+  float2* pub;   // [2][2][m]: per parity, a_jj and a_{partner(j), j}
+  double* nrm2;  // [n] squared column norms of V
+  double* red;   // 2 * gridDim.x partial norms
+  unsigned* bar;
+  int* status;   // [0] 1 = no convergence, [1] 1 = barrier wait expired, [2] sweeps
+  int max_sweeps;
+};
+
+// the round that follows round r of sweep `sw` (the next sweep starts at round 0)
+__device__ __forceinline__ int next_round(int r, int m) { return r + 1 < m - 1 ? r + 1 : 0; }
+
+__global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
+  extern __shared__ float4 s_rot[];                              // [half]
+  int2* s_pair = reinterpret_cast<int2*>(s_rot + P.half);       // [half]
+  float2* colP = reinterpret_cast<float2*>(s_pair + P.half);   // [n]
+  float2* colQ = colP + P.n;                                     // [n]
+  const int n = P.n, m = P.m, half = P.half;
+  const long n2 = (long)n * n;
+  // ---- set-up: A (symmetrised) and V = 1 in columns, round 0's inputs
+  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+    const int j = (int)(idx / n), i = (int)(idx % n);
+    const dd a = dd_from_double(0.5 * (P.A_in[(long)i * n + j] + P.A_in[(long)j * n + i]));
+    P.Ac[idx] = make_float2(a.hi, a.lo);
+    P.Vc[idx] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
+  }
+  for (int j = blockIdx.x * JNT + threadIdx.x; j < n; j += gridDim.x * JNT) {
+    const int pos = rr_position(j, 0, m);
+    const int pj = rr_index(m - 1 - pos, 0, m);
+    const double a = 0.5 * (P.A_in[(long)j * n + j] + P.A_in[(long)j * n + j]);
+    const dd djj = dd_from_double(a);
+    dd off = dd_make(0.0f);
+    if (pj < n) off = dd_from_double(0.5 * (P.A_in[(long)pj * n + j] + P.A_in[(long)j * n + pj]));
+    P.pub[j] = make_float2(djj.hi, djj.lo);
+    P.pub[m + j] = make_float2(off.hi, off.lo);
+  }
+  if (!grid_barrier_at(P.bar, P.status)) return;
+  const double tol = fmax(1e-30, ((double)n * 4e-15) * ((double)n * 4e-15));
+  double prev = -1.0;
+  int converged = 0, sweeps_done = 0, cur = 0;
+  for (int sweep = 0; sweep <= P.max_sweeps; ++sweep) {
+    sweeps_done = sweep;
+    // ---- convergence: off-diagonal and total squared norms (fixed order)
+    {
+      __shared__ double s_o[JNT], s_t[JNT];
+      double o = 0.0, t = 0.0;
+      for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+        const float2 v = __ldcg(P.Ac + idx);
+        const double a = (double)v.x + (double)v.y;
+        t += a * a;
+        if (idx / n != idx % n) o += a * a;
+      }
+      s_o[threadIdx.x] = o;
+      s_t[threadIdx.x] = t;
+      __syncthreads();
+      for (int w = JNT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+          s_o[threadIdx.x] += s_o[threadIdx.x + w];
+          s_t[threadIdx.x] += s_t[threadIdx.x + w];
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        __stcg(P.red + 2 * blockIdx.x, s_o[0]);
+        __stcg(P.red + 2 * blockIdx.x + 1, s_t[0]);
+      }
+      if (!grid_barrier_at(P.bar, P.status)) return;
+      double so = 0.0, st = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        so += __ldcg(P.red + 2 * b);
+        st += __ldcg(P.red + 2 * b + 1);
+      }
+      if (st == 0.0 || so <= tol * st || (so <= 1e-22 * st && prev >= 0.0 && so > 0.25 * prev)) {
+        converged = 1;
+        break;
+      }
+      prev = so;
+      if (sweep == P.max_sweeps) break;
+    }
+    for (int r = 0; r < m - 1; ++r) {
+      const float2* pd = P.pub + (size_t)cur * 2 * m;      // a_jj
+      const float2* po = pd + m;                             // a_{partner(j), j}
+      // ---- all rotations of this round, from the published entries
+      for (int k = threadIdx.x; k < half; k += JNT) {
+        const int i1 = rr_index(k, r, m), i2 = rr_index(m - 1 - k, r, m);
+        const int p = min(i1, i2), q = max(i1, i2);
+        float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (q < n) {
+          const float2 dp = __ldcg(pd + p), dq = __ldcg(pd + q), op = __ldcg(po + p), oq = __ldcg(po + q);
+          const dd apq = dd_mul_f(dd_add(dd{op.x, op.y}, dd{oq.x, oq.y}), 0.5f);
+          cs = jacobi_rotation(dd{dp.x, dp.y}, dd{dq.x, dq.y}, apq);
+        }
+        s_rot[k] = cs;
+        s_pair[k] = make_int2(p, q);
+      }
+      __syncthreads();
+      float2* nd = P.pub + (size_t)(cur ^ 1) * 2 * m;
+      float2* no = nd + m;
+      const int rn = next_round(r, m);
+      for (int kk = 0; kk < P.cp; ++kk) {
+        const int k = blockIdx.x * P.cp + kk;
+        if (k >= half) break;
+        const int2 pq = s_pair[k];
+        const int p = pq.x, q = pq.y;
+        const float4 cc = s_rot[k];
+        const dd c = {cc.x, cc.y}, sn = {cc.z, cc.w};
+        const bool qr = q < n;
+        // M = A J on columns p, q
+        for (int i = threadIdx.x; i < n; i += JNT) {
+          const float2 a = __ldcg(P.Ac + (long)p * n + i);
+          const dd ap = {a.x, a.y};
+          if (qr) {
+            const float2 b = __ldcg(P.Ac + (long)q * n + i);
+            const dd aq = {b.x, b.y};
+            const dd mp = rot_combine(c, ap, sn, aq, true), mq = rot_combine(sn, ap, c, aq, false);
+            colP[i] = make_float2(mp.hi, mp.lo);
+            colQ[i] = make_float2(mq.hi, mq.lo);
+          } else {
+            colP[i] = a;
+          }
+        }
+        // V J on columns p, q (rows are independent)
+        if (qr) {
+          for (int i = threadIdx.x; i < n; i += JNT) {
+            const float2 a = __ldcg(P.Vc + (long)p * n + i), b = __ldcg(P.Vc + (long)q * n + i);
+            const dd vp = {a.x, a.y}, vq = {b.x, b.y};
+            const dd wp = rot_combine(c, vp, sn, vq, true), wq = rot_combine(sn, vp, c, vq, false);
+            __stcg(P.Vc + (long)p * n + i, make_float2(wp.hi, wp.lo));
+            __stcg(P.Vc + (long)q * n + i, make_float2(wq.hi, wq.lo));
+          }
+        }
+        __syncthreads();
+        // A' = J^T M: every row pair of the round, in place in colP / colQ
+        for (int k2 = threadIdx.x; k2 < half; k2 += JNT) {
+          const int2 rq = s_pair[k2];
+          if (rq.y >= n) continue;
+          const float4 rc = s_rot[k2];
+          const dd cr = {rc.x, rc.y}, sr = {rc.z, rc.w};
+          {
+            const float2 x = colP[rq.x], y = colP[rq.y];
+            const dd xp = {x.x, x.y}, yq = {y.x, y.y};
+            const dd u = rot_combine(cr, xp, sr, yq, true), v = rot_combine(sr, xp, cr, yq, false);
+            colP[rq.x] = make_float2(u.hi, u.lo);
+            colP[rq.y] = make_float2(v.hi, v.lo);
+          }
+          if (qr) {
+            const float2 x = colQ[rq.x], y = colQ[rq.y];
+            const dd xp = {x.x, x.y}, yq = {y.x, y.y};
+            const dd u = rot_combine(cr, xp, sr, yq, true), v = rot_combine(sr, xp, cr, yq, false);
+            colQ[rq.x] = make_float2(u.hi, u.lo);
+            colQ[rq.y] = make_float2(v.hi, v.lo);
+          }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += JNT) {
+          __stcg(P.Ac + (long)p * n + i, colP[i]);
+          if (qr) __stcg(P.Ac + (long)q * n + i, colQ[i]);
+        }
+        // the next round's inputs of columns p and q
+        if (threadIdx.x == 0) {
+          const int pp = rr_index(m - 1 - rr_position(p, rn, m), rn, m);
+          __stcg(nd + p, colP[p]);
+          __stcg(no + p, pp < n ? colP[pp] : make_float2(0.f, 0.f));
+          if (qr) {
+            const int qq = rr_index(m - 1 - rr_position(q, rn, m), rn, m);
+            __stcg(nd + q, colQ[q]);
+            __stcg(no + q, qq < n ? colQ[qq] : make_float2(0.f, 0.f));
+          }
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier_at(P.bar, P.status)) return;
+      cur ^= 1;
+    }
+  }
+  // ---- output: Rayleigh quotients and eigenvectors normalised by the
+  // column norms of V (they drift from 1 by rounding of the rotations)
+  double* nrm2 = P.nrm2;
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    __shared__ double s_r[JNT];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += JNT) {
+      const float2 v = __ldcg(P.Vc + (long)j * n + i);
+      const dd vv = dd_mul(dd{v.x, v.y}, dd{v.x, v.y});
+      acc += dd_to_double(vv);
+    }
+    s_r[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = JNT / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) s_r[threadIdx.x] += s_r[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) __stcg(nrm2 + j, s_r[0]);
+    __syncthreads();
+  }
+  if (!grid_barrier_at(P.bar, P.status)) return;
+  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    const float2 a = __ldcg(P.Ac + (long)j * n + i), v = __ldcg(P.Vc + (long)j * n + i);
+    const double nj = __ldcg(nrm2 + j), ni = __ldcg(nrm2 + i);
+    P.A_out[idx] = ((double)a.x + (double)a.y) / (i == j ? nj : sqrt(nj * ni));
+    P.V_out[idx] = ((double)v.x + (double)v.y) / sqrt(nj);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.status[0] = converged ? 0 : 1;
+    P.status[2] = sweeps_done;
+  }
+}
+
 // ranks by (value descending | ascending, index ascending)
 __global__ void eig_rank_kernel(int n, const double* __restrict__ A, bool descending, int* rank) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,6 +645,54 @@ SharedDeviceScope::~SharedDeviceScope() { t_device_shared = prev; }
 // A (n x n, symmetric) is destroyed: on return its diagonal holds the
 // eigenvalues; V (n x n) receives the eigenvectors (column j <-> A[j][j]).
 // work: eig_work_doubles(n) doubles.  status_dev: four ints of device memory.
+// Matrices above the shared-memory size: the column-pair kernel (default) or
+// the round-parallel kernel over A in global memory (test hook, comparison).
+static std::atomic<int> g_eig_colpair{1};
+void set_eig_colpair(bool on) { g_eig_colpair.store(on ? 1 : 0); }
+
+static int eig_colpair(int n, int m, double* A, double* V, double* work, int* status_dev, int max_sweeps,
+                       cudaStream_t st) {
+  const long n2 = (long)n * n;
+  ColPairArgs P;
+  P.n = n;
+  P.m = m;
+  P.half = m / 2;
+  P.A_in = A;
+  P.A_out = A;
+  P.V_out = V;
+  P.Ac = reinterpret_cast<float2*>(work);
+  P.Vc = reinterpret_cast<float2*>(work + 2 * n2);
+  P.pub = reinterpret_cast<float2*>(work + n2);
+  P.nrm2 = work + n2 + 4 * (long)m + 16;
+  P.red = work + 3 * n2;
+  P.bar = reinterpret_cast<unsigned*>(work + 3 * n2 + 2 * JMAX_BLOCKS);
+  P.status = status_dev;
+  P.max_sweeps = max_sweeps;
+  const size_t smem = (sizeof(float4) + sizeof(int2)) * (size_t)P.half + 2 * sizeof(float2) * (size_t)n;
+  if (smem > (size_t)200 * 1024 || n2 < 4 * (long)m + 16 + n) return DSRG_FNO_ERR_UNSUPPORTED;
+  auto kern = jacobi_colpair_kernel;
+  if (smem > 48 * 1024) DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  int dev = 0, sms = 0, occ = 0;
+  DSRG_CUDA(cudaGetDevice(&dev));
+  DSRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, JNT, smem));
+  if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
+  // on a device shared with other batch workers, at most one block per SM
+  const int per_sm = t_device_shared ? 1 : occ;
+  const int G = std::max(1, std::min(std::min(sms * per_sm, JMAX_BLOCKS), P.half));
+  P.cp = (P.half + G - 1) / G;
+  const int grid = (P.half + P.cp - 1) / P.cp;
+  void* args[] = {&P};
+  DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(JNT), args, smem, st));
+  DSRG_LAUNCH_CHECK();
+  int h[3] = {0, 0, 0};
+  DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  prof_count(n >= 256 ? "eig_sweeps_large" : "eig_sweeps_small", (double)h[2]);
+  if (h[1]) return DSRG_FNO_ERR_TIMEOUT;
+  return h[0] ? DSRG_FNO_ERR_NOCONV : DSRG_FNO_OK;
+}
+
 // Spin limit of the grid barrier on the current device; spins <= 0 restores
 // the default (test hook: a tiny limit makes the barrier's wait run out).
 int eig_set_barrier_limit(long long spins) {
@@ -430,6 +730,7 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   if (smem > (size_t)SMEM_CEILING) return DSRG_FNO_ERR_UNSUPPORTED;
   // one fixed ceiling for every launch: concurrent callers (batch workers)
   // never lower it under one another
+  if (!in_smem && g_eig_colpair.load()) return eig_colpair(n, m, A, V, work, status_dev, max_sweeps, st);
   auto kern = in_smem ? jacobi_coop_kernel<true> : jacobi_coop_kernel<false>;
   if (smem > 48 * 1024)
     DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CEILING));

@@ -72,6 +72,7 @@ int syrk_dressed_f64(int nv, int nr, const double* sig, const double* sig_sign, 
 constexpr int EIG_MAX_BLOCKS = 1024;  // grid bound of the eigensolver (reduction scratch)
 constexpr size_t eig_work_doubles(int n) { return 3 * (size_t)n * n + 2 * EIG_MAX_BLOCKS + 16; }
 int eig_set_barrier_limit(long long spins);
+void set_eig_colpair(bool on);
 int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
                    cudaStream_t st);
 // Marks the calling thread, for the scope's lifetime, as one of several host
@@ -150,6 +151,7 @@ int stage_literal(int form, int KS, const double* src, long R, int K, long rs, l
 int eps_to_dd(int n, const double* eps, float2* out, cudaStream_t st);
 int reg_tables_device(const RegTables** out);
 bool fused_epilogue_enabled();
+void set_syrk_planes(int k);
 void set_fused_epilogue(bool on);
 int hole_particle_dd(const Geometry& g, const double* eps, float2* out, cudaStream_t st);
 int pair_epilogue_dd(const Geometry& g, const double* eps, const float2* eps_dd, const int2* pairs, int npairs,

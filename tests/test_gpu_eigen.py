@@ -105,3 +105,20 @@ def test_grid_barrier_timeout_is_reported_and_the_next_solve_is_clean():
         pkg.dsrg_fno_debug_set_barrier_limit(0)
     ons, nos = solve(D)
     check(D, ons, nos)
+
+
+@pytest.mark.parametrize("colpair", [True, False], ids=["colpair", "round_parallel"])
+@pytest.mark.parametrize("n", [81, 300, 1001])
+def test_both_multi_block_kernels_against_lapack(colpair, n):
+    """Above the one-block size both Jacobi organisations (column pairs, the
+    default; round-parallel over A in global memory) reproduce LAPACK on a
+    spectrum with a tight cluster and a wide spread of magnitudes."""
+    rng = np.random.default_rng(n + 7)
+    lam = np.concatenate([np.geomspace(2.0, 1e-7, n - 6), 0.5 + 1e-9 * np.arange(6)])
+    D = with_spectrum(rng, lam)
+    pkg.dsrg_fno_debug_set_eig_colpair(colpair)
+    try:
+        ons, nos = solve(D)
+    finally:
+        pkg.dsrg_fno_debug_set_eig_colpair(True)
+    check(D, ons, nos)

@@ -4,7 +4,8 @@ The oracle cannot rerun the full-size workloads inside a test (nvir 1200 takes
 about an hour on eight cores), so tests/golden/make_golden.py stored its
 results once; here the CUDA path, in both arithmetic forms and in the launch
 configuration the benchmark uses, is compared with them: E_vv, every ON,
-diag and row 0 of D_vv, N' and the correction of every cut.
+diag and row 0 of D_vv (and its products with seeded probe vectors where
+stored), N' and the correction of every cut.
 """
 import functools
 import glob
@@ -65,6 +66,10 @@ def test_workload_matches_stored_oracle(path, precision):
     dmax = np.abs(np.array(ref["dvv_diag"])).max()
     assert np.abs(np.diag(got["dvv"]) - np.array(ref["dvv_diag"])).max() <= 1e-9 * dmax
     assert np.abs(got["dvv"][0] - np.array(ref["dvv_row0"])).max() <= 1e-9 * dmax
+    if "dvv_probe" in ref:   # D_vv applied to seeded normal vectors: every element enters
+        R = np.random.default_rng(ref["probe_seed"]).standard_normal((p.nvir, ref["probes"]))
+        pr = (got["dvv"] @ R).T
+        assert np.abs(pr - np.array(ref["dvv_probe"])).max() <= 1e-9 * dmax * np.sqrt(p.nvir)
     for c in cuts:
         k, de, ef = got["cuts"][c]
         r = ref["cuts"][str(c)] if str(c) in ref["cuts"] else ref["cuts"][repr(c)]
