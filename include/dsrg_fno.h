@@ -215,9 +215,9 @@ int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_t mode, dou
  *   T          device [npairs][nv][nv]: T[p][c][d] = T^{ij}_{cd} of hole pair p.
  *   precision  DSRG_FNO_FP64 or DSRG_FNO_SLICED_BF16 (5 digit planes).
  *   C_out      device [npairs][nv][nv].
- * The 4-index integrals are formed for 8 values of a at a time and never
+ * The 4-index integrals are formed for 16 values of a at a time and never
  * stored whole.  Errors: DSRG_FNO_ERR_ARG for bad sizes, null or host
- * pointers; sizes with nv^3 * 8 or npairs * nv^2 >= 2^31 and other
+ * pointers; sizes with nv^3 * 16 or npairs * nv^2 >= 2^31 and other
  * precisions give DSRG_FNO_ERR_UNSUPPORTED. */
 int dsrg_fno_ladder(int32_t nv, int32_t naux, const double* B_vv, int32_t npairs, const double* T,
                     int32_t precision, double* C_out, void* stream);

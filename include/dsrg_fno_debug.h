@@ -74,9 +74,8 @@ int dsrg_fno_debug_set_barrier_limit(int64_t spins);
 int dsrg_fno_debug_set_fused_epilogue(int32_t on);
 
 /* Digit planes of the dressed matrices in the fast form's rank-K update of
- * D_vv: 0 (default) = 4 when the problem uses 5 planes, else the problem's
- * count; 3..5 = that many (at most the problem's count).  Affects later
- * calls of this process. */
+ * D_vv: 0 (default) = the problem's count; 3..5 = that many (at most the
+ * problem's count).  Affects later calls of this process. */
 int dsrg_fno_debug_set_syrk_planes(int32_t nslices);
 
 /* on != 0 (the default): symmetric eigensolves above 80 x 80 run on the

@@ -232,18 +232,17 @@ static int slices_of(const dsrg_fno_problem* p) {
   return p->nslices ? p->nslices : DEFAULT_SLICES;
 }
 
-// Digit planes of the dressed matrices in the rank-K update of D_vv.  They
-// enter D_vv only (never an energy): with 4 planes (31 fraction bits) the
-// first dropped level, biased on D's diagonal by its square term, is about
-// 2^-32 of D, 4e-10 of an occupation number of ~2, against the 1e-8
-// tolerance, for two thirds of the digit products of 5 planes.  A test hook
-// can set the count (0 = this rule).
+// Digit planes of the dressed matrices in the rank-K update of D_vv: those
+// of the problem, unless a test hook sets fewer.  (4 planes, which would save
+// a third of the update's digit products, were measured to miss the 1e-8
+// tolerance on the occupation numbers: 1.8e-8 on the single-reference nvir 90
+// workload, whose dressed rows hold elements far below their row maximum.)
 static std::atomic<int> g_syrk_planes{0};
 void set_syrk_planes(int k) { g_syrk_planes.store(k); }
 static int syrk_slices(int ks) {
   const int f = g_syrk_planes.load();
   if (f >= 3 && f <= 5) return std::min(f, ks);
-  return ks >= 5 ? 4 : ks;
+  return ks;
 }
 
 // Form and parts of the B.B contraction: {FORM_DIGITS, ks}, {FORM_BF16X3, 2},

@@ -370,7 +370,7 @@ __device__ __forceinline__ int rr_position(int j, int r, int m) {
 // forms all rotations of the next round: one grid barrier per round, the
 // matrix moving through L2 once per round.
 struct ColPairArgs {
-  int n, m, half, cp;
+  int n, m, half, cp, cpc;  // pairs per block, pairs held in shared memory at a time
   const double* A_in;
   double* A_out;
   double* V_out;
@@ -384,24 +384,27 @@ struct ColPairArgs {
   int max_sweeps;
 };
 
+// threads per block of the column-pair kernel: one block per SM, so the
+// latency of its column loads is hidden by the warps of that one block
+constexpr int CPT = 1024;
+
 // the round that follows round r of sweep `sw` (the next sweep starts at round 0)
 __device__ __forceinline__ int next_round(int r, int m) { return r + 1 < m - 1 ? r + 1 : 0; }
 
-__global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
+__global__ void __launch_bounds__(CPT) jacobi_colpair_kernel(ColPairArgs P) {
   extern __shared__ float4 s_rot[];                              // [half]
   int2* s_pair = reinterpret_cast<int2*>(s_rot + P.half);       // [half]
-  float2* colP = reinterpret_cast<float2*>(s_pair + P.half);   // [n]
-  float2* colQ = colP + P.n;                                     // [n]
+  float2* colP = reinterpret_cast<float2*>(s_pair + P.half);   // [2 cpc][n]: p and q columns of each pair
   const int n = P.n, m = P.m, half = P.half;
   const long n2 = (long)n * n;
   // ---- set-up: A (symmetrised) and V = 1 in columns, round 0's inputs
-  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+  for (long idx = blockIdx.x * (long)CPT + threadIdx.x; idx < n2; idx += (long)gridDim.x * CPT) {
     const int j = (int)(idx / n), i = (int)(idx % n);
     const dd a = dd_from_double(0.5 * (P.A_in[(long)i * n + j] + P.A_in[(long)j * n + i]));
     P.Ac[idx] = make_float2(a.hi, a.lo);
     P.Vc[idx] = make_float2(i == j ? 1.0f : 0.0f, 0.0f);
   }
-  for (int j = blockIdx.x * JNT + threadIdx.x; j < n; j += gridDim.x * JNT) {
+  for (int j = blockIdx.x * CPT + threadIdx.x; j < n; j += gridDim.x * CPT) {
     const int pos = rr_position(j, 0, m);
     const int pj = rr_index(m - 1 - pos, 0, m);
     const double a = 0.5 * (P.A_in[(long)j * n + j] + P.A_in[(long)j * n + j]);
@@ -419,9 +422,9 @@ __global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
     sweeps_done = sweep;
     // ---- convergence: off-diagonal and total squared norms (fixed order)
     {
-      __shared__ double s_o[JNT], s_t[JNT];
+      __shared__ double s_o[CPT], s_t[CPT];
       double o = 0.0, t = 0.0;
-      for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+      for (long idx = blockIdx.x * (long)CPT + threadIdx.x; idx < n2; idx += (long)gridDim.x * CPT) {
         const float2 v = __ldcg(P.Ac + idx);
         const double a = (double)v.x + (double)v.y;
         t += a * a;
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
       s_o[threadIdx.x] = o;
       s_t[threadIdx.x] = t;
       __syncthreads();
-      for (int w = JNT / 2; w > 0; w >>= 1) {
+      for (int w = CPT / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
           s_o[threadIdx.x] += s_o[threadIdx.x + w];
           s_t[threadIdx.x] += s_t[threadIdx.x + w];
@@ -458,7 +461,7 @@ __global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
       const float2* pd = P.pub + (size_t)cur * 2 * m;      // a_jj
       const float2* po = pd + m;                             // a_{partner(j), j}
       // ---- all rotations of this round, from the published entries
-      for (int k = threadIdx.x; k < half; k += JNT) {
+      for (int k = threadIdx.x; k < half; k += CPT) {
         const int i1 = rr_index(k, r, m), i2 = rr_index(m - 1 - k, r, m);
         const int p = min(i1, i2), q = max(i1, i2);
         float4 cs = make_float4(1.f, 0.f, 0.f, 0.f);
@@ -474,75 +477,68 @@ __global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
       float2* nd = P.pub + (size_t)(cur ^ 1) * 2 * m;
       float2* no = nd + m;
       const int rn = next_round(r, m);
-      for (int kk = 0; kk < P.cp; ++kk) {
-        const int k = blockIdx.x * P.cp + kk;
-        if (k >= half) break;
-        const int2 pq = s_pair[k];
-        const int p = pq.x, q = pq.y;
-        const float4 cc = s_rot[k];
-        const dd c = {cc.x, cc.y}, sn = {cc.z, cc.w};
-        const bool qr = q < n;
-        // M = A J on columns p, q
-        for (int i = threadIdx.x; i < n; i += JNT) {
-          const float2 a = __ldcg(P.Ac + (long)p * n + i);
-          const dd ap = {a.x, a.y};
-          if (qr) {
-            const float2 b = __ldcg(P.Ac + (long)q * n + i);
-            const dd aq = {b.x, b.y};
+      const int k0 = blockIdx.x * P.cp;
+      const int kend = min(k0 + P.cp, half);
+      // this block's pairs, P.cpc at a time (as many as shared memory holds)
+      for (int kb = k0; kb < kend; kb += P.cpc) {
+        const int nk = min(P.cpc, kend - kb);
+        // M = A J on columns p, q of each pair (colP / colQ rows of length n)
+        for (int idx = threadIdx.x; idx < nk * n; idx += CPT) {
+          const int kk = idx / n, i = idx - kk * n;
+          const int2 pq = s_pair[kb + kk];
+          const float4 cc = s_rot[kb + kk];
+          const dd c = {cc.x, cc.y}, sn = {cc.z, cc.w};
+          const float2 a = __ldcg(P.Ac + (long)pq.x * n + i);
+          float2* cP = colP + (size_t)kk * 2 * n;
+          if (pq.y < n) {
+            const float2 b = __ldcg(P.Ac + (long)pq.y * n + i);
+            const dd ap = {a.x, a.y}, aq = {b.x, b.y};
             const dd mp = rot_combine(c, ap, sn, aq, true), mq = rot_combine(sn, ap, c, aq, false);
-            colP[i] = make_float2(mp.hi, mp.lo);
-            colQ[i] = make_float2(mq.hi, mq.lo);
-          } else {
-            colP[i] = a;
-          }
-        }
-        // V J on columns p, q (rows are independent)
-        if (qr) {
-          for (int i = threadIdx.x; i < n; i += JNT) {
-            const float2 a = __ldcg(P.Vc + (long)p * n + i), b = __ldcg(P.Vc + (long)q * n + i);
-            const dd vp = {a.x, a.y}, vq = {b.x, b.y};
+            cP[i] = make_float2(mp.hi, mp.lo);
+            cP[n + i] = make_float2(mq.hi, mq.lo);
+            // V J on the same columns (rows are independent)
+            const float2 va = __ldcg(P.Vc + (long)pq.x * n + i), vb = __ldcg(P.Vc + (long)pq.y * n + i);
+            const dd vp = {va.x, va.y}, vq = {vb.x, vb.y};
             const dd wp = rot_combine(c, vp, sn, vq, true), wq = rot_combine(sn, vp, c, vq, false);
-            __stcg(P.Vc + (long)p * n + i, make_float2(wp.hi, wp.lo));
-            __stcg(P.Vc + (long)q * n + i, make_float2(wq.hi, wq.lo));
+            __stcg(P.Vc + (long)pq.x * n + i, make_float2(wp.hi, wp.lo));
+            __stcg(P.Vc + (long)pq.y * n + i, make_float2(wq.hi, wq.lo));
+          } else {
+            cP[i] = a;
           }
         }
         __syncthreads();
-        // A' = J^T M: every row pair of the round, in place in colP / colQ
-        for (int k2 = threadIdx.x; k2 < half; k2 += JNT) {
+        // A' = J^T M: every row pair of the round, on every loaded column, in place
+        for (int idx = threadIdx.x; idx < nk * 2 * half; idx += CPT) {
+          const int col = idx / half, k2 = idx - col * half;   // col: 2 kk + (0: p, 1: q)
+          const int kk = col >> 1;
+          if ((col & 1) && s_pair[kb + kk].y >= n) continue;
           const int2 rq = s_pair[k2];
           if (rq.y >= n) continue;
           const float4 rc = s_rot[k2];
           const dd cr = {rc.x, rc.y}, sr = {rc.z, rc.w};
-          {
-            const float2 x = colP[rq.x], y = colP[rq.y];
-            const dd xp = {x.x, x.y}, yq = {y.x, y.y};
-            const dd u = rot_combine(cr, xp, sr, yq, true), v = rot_combine(sr, xp, cr, yq, false);
-            colP[rq.x] = make_float2(u.hi, u.lo);
-            colP[rq.y] = make_float2(v.hi, v.lo);
-          }
-          if (qr) {
-            const float2 x = colQ[rq.x], y = colQ[rq.y];
-            const dd xp = {x.x, x.y}, yq = {y.x, y.y};
-            const dd u = rot_combine(cr, xp, sr, yq, true), v = rot_combine(sr, xp, cr, yq, false);
-            colQ[rq.x] = make_float2(u.hi, u.lo);
-            colQ[rq.y] = make_float2(v.hi, v.lo);
-          }
+          float2* cc = colP + (size_t)col * n;
+          const float2 x = cc[rq.x], y = cc[rq.y];
+          const dd xp = {x.x, x.y}, yq = {y.x, y.y};
+          const dd u = rot_combine(cr, xp, sr, yq, true), v = rot_combine(sr, xp, cr, yq, false);
+          cc[rq.x] = make_float2(u.hi, u.lo);
+          cc[rq.y] = make_float2(v.hi, v.lo);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += JNT) {
-          __stcg(P.Ac + (long)p * n + i, colP[i]);
-          if (qr) __stcg(P.Ac + (long)q * n + i, colQ[i]);
+        for (int idx = threadIdx.x; idx < nk * 2 * n; idx += CPT) {
+          const int col = idx / n, i = idx - col * n;
+          const int2 pq = s_pair[kb + (col >> 1)];
+          const int j = (col & 1) ? pq.y : pq.x;
+          if (j < n) __stcg(P.Ac + (long)j * n + i, colP[(size_t)col * n + i]);
         }
-        // the next round's inputs of columns p and q
-        if (threadIdx.x == 0) {
-          const int pp = rr_index(m - 1 - rr_position(p, rn, m), rn, m);
-          __stcg(nd + p, colP[p]);
-          __stcg(no + p, pp < n ? colP[pp] : make_float2(0.f, 0.f));
-          if (qr) {
-            const int qq = rr_index(m - 1 - rr_position(q, rn, m), rn, m);
-            __stcg(nd + q, colQ[q]);
-            __stcg(no + q, qq < n ? colQ[qq] : make_float2(0.f, 0.f));
-          }
+        // the next round's inputs of the loaded columns
+        for (int col = threadIdx.x; col < 2 * nk; col += CPT) {
+          const int2 pq = s_pair[kb + (col >> 1)];
+          const int j = (col & 1) ? pq.y : pq.x;
+          if (j >= n) continue;
+          const float2* cc = colP + (size_t)col * n;
+          const int pj = rr_index(m - 1 - rr_position(j, rn, m), rn, m);
+          __stcg(nd + j, cc[j]);
+          __stcg(no + j, pj < n ? cc[pj] : make_float2(0.f, 0.f));
         }
         __syncthreads();
       }
@@ -554,16 +550,16 @@ __global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
   // column norms of V (they drift from 1 by rounding of the rotations)
   double* nrm2 = P.nrm2;
   for (int j = blockIdx.x; j < n; j += gridDim.x) {
-    __shared__ double s_r[JNT];
+    __shared__ double s_r[CPT];
     double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += JNT) {
+    for (int i = threadIdx.x; i < n; i += CPT) {
       const float2 v = __ldcg(P.Vc + (long)j * n + i);
       const dd vv = dd_mul(dd{v.x, v.y}, dd{v.x, v.y});
       acc += dd_to_double(vv);
     }
     s_r[threadIdx.x] = acc;
     __syncthreads();
-    for (int w = JNT / 2; w > 0; w >>= 1) {
+    for (int w = CPT / 2; w > 0; w >>= 1) {
       if (threadIdx.x < w) s_r[threadIdx.x] += s_r[threadIdx.x + w];
       __syncthreads();
     }
@@ -571,7 +567,7 @@ __global__ void __launch_bounds__(JNT) jacobi_colpair_kernel(ColPairArgs P) {
     __syncthreads();
   }
   if (!grid_barrier_at(P.bar, P.status)) return;
-  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+  for (long idx = blockIdx.x * (long)CPT + threadIdx.x; idx < n2; idx += (long)gridDim.x * CPT) {
     const int i = (int)(idx / n), j = (int)(idx % n);
     const float2 a = __ldcg(P.Ac + (long)j * n + i), v = __ldcg(P.Vc + (long)j * n + i);
     const double nj = __ldcg(nrm2 + j), ni = __ldcg(nrm2 + i);
@@ -668,22 +664,29 @@ static int eig_colpair(int n, int m, double* A, double* V, double* work, int* st
   P.bar = reinterpret_cast<unsigned*>(work + 3 * n2 + 2 * JMAX_BLOCKS);
   P.status = status_dev;
   P.max_sweeps = max_sweeps;
-  const size_t smem = (sizeof(float4) + sizeof(int2)) * (size_t)P.half + 2 * sizeof(float2) * (size_t)n;
-  if (smem > (size_t)200 * 1024 || n2 < 4 * (long)m + 16 + n) return DSRG_FNO_ERR_UNSUPPORTED;
+  const size_t table = (sizeof(float4) + sizeof(int2)) * (size_t)P.half;
+  const size_t per_pair = 2 * sizeof(float2) * (size_t)n;
+  const size_t cap = 200 * 1024;
+  if (table + per_pair > cap || n2 < 4 * (long)m + 16 + n) return DSRG_FNO_ERR_UNSUPPORTED;
   auto kern = jacobi_colpair_kernel;
-  if (smem > 48 * 1024) DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  int dev = 0, sms = 0, occ = 0;
+  int dev = 0, sms = 0;
   DSRG_CUDA(cudaGetDevice(&dev));
   DSRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, JNT, smem));
-  if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
-  // on a device shared with other batch workers, at most one block per SM
-  const int per_sm = t_device_shared ? 1 : occ;
-  const int G = std::max(1, std::min(std::min(sms * per_sm, JMAX_BLOCKS), P.half));
+  // one block per SM: a round ends in a grid barrier whose arrivals are
+  // serialised atomics, so more blocks make every round slower; the pairs of
+  // a block are rotated together, as many at a time as shared memory holds
+  // (half the SMs when batch workers share the device: their solves overlap)
+  const int G = std::max(1, std::min(std::min(t_device_shared ? sms / 2 : sms, JMAX_BLOCKS), P.half));
   P.cp = (P.half + G - 1) / G;
+  P.cpc = (int)std::max<size_t>(1, std::min<size_t>((size_t)P.cp, (cap - table) / per_pair));
+  const size_t smem = table + per_pair * (size_t)P.cpc;
+  if (smem > 48 * 1024) DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+  int occ = 0;
+  DSRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, CPT, smem));
+  if (occ < 1) return DSRG_FNO_ERR_UNSUPPORTED;
   const int grid = (P.half + P.cp - 1) / P.cp;
   void* args[] = {&P};
-  DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(JNT), args, smem, st));
+  DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(CPT), args, smem, st));
   DSRG_LAUNCH_CHECK();
   int h[3] = {0, 0, 0};
   DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -30,7 +30,7 @@ __global__ void swap_middle_kernel(int A, int nv, const double* __restrict__ in,
 
 }  // namespace
 
-static const int LADDER_A_BLK = 8;
+static const int LADDER_A_BLK = 16;
 
 int impl_ladder(Workspace& ws, int32_t nv, int32_t naux, const double* Bvv, int32_t npairs, const double* T,
                 int32_t precision, double* C, cudaStream_t st) {

@@ -118,33 +118,3 @@ def test_fused_epilogue_equals_the_separate_kernel(shape):
     assert np.max(np.abs(d1 - d0)) <= 1e-12 * np.max(np.abs(d0))
     assert abs(e1 - ref["e2"]) <= E_TOL
     assert np.max(np.abs(d1 - ref["dvv"])) <= 1e-9 * np.max(np.abs(ref["dvv"]))
-
-
-def test_rank_k_update_with_four_planes():
-    """The dressed matrices of the rank-K update in 4 digit planes (the
-    default with 5-plane contractions) against 5: D_vv agrees to 1e-9 of its
-    largest element, the ONs to 1e-9, E_vv exactly (the update does not enter
-    the energy), and both match the oracle."""
-    p = make_problem(ncore=7, nact=4, nvir=230, naux=500, seed=49, nstates=3)
-    ref = O.solve(p, cuts=(98.5,))
-    gp = pkg.problem_from_synth(p, "cuda", pkg.SLICED_BF16, 5)
-    nv = p.nvir
-    out = {}
-    try:
-        for k in (5, 4):
-            pkg.dsrg_fno_debug_set_syrk_planes(k)
-            d = torch.empty((nv, nv), dtype=torch.float64, device="cuda")
-            e2 = pkg.dsrg_fno_vv_opdm(gp, d)
-            on = torch.empty(nv, dtype=torch.float64, device="cuda")
-            no = torch.empty((nv, nv), dtype=torch.float64, device="cuda")
-            kk = pkg.dsrg_fno_truncate(nv, d, pkg.MODE_PO, 98.5, 0.01, on, no)
-            out[k] = (e2, d.cpu().numpy(), on.cpu().numpy(), kk)
-    finally:
-        pkg.dsrg_fno_debug_set_syrk_planes(0)
-    (e5, d5, on5, k5), (e4, d4, on4, k4) = out[5], out[4]
-    dmax = np.max(np.abs(ref["dvv"]))
-    print("4 vs 5 planes: max |dD| / max|D|", np.max(np.abs(d4 - d5)) / dmax, "max |dON|", np.max(np.abs(on4 - on5)))
-    assert e4 == e5 and k4 == k5 == ref["cuts"][98.5]["nkept"]
-    assert np.max(np.abs(d4 - d5)) <= 1e-9 * dmax
-    assert np.max(np.abs(on4 - on5)) <= 1e-9
-    assert np.max(np.abs(d4 - ref["dvv"])) <= 1e-9 * dmax and np.max(np.abs(on4 - ref["ons"])) <= ON_TOL
