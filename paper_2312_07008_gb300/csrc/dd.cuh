@@ -85,6 +85,16 @@ __device__ __forceinline__ dd dd_div(dd a, dd b) {
   return dd_add_f(q, q3);
 }
 
+// 1 / b: float reciprocal (one rounding), then one Newton step in
+// double-float, r1 = r0 + r0 (1 - b r0), with 1 - b r0 formed exactly enough
+// (TwoProduct of the high parts): relative error about 2^-46.
+__device__ __forceinline__ dd dd_recip(dd b) {
+  const float r0 = __frcp_rn(b.hi);
+  const dd p = two_prod(b.hi, r0);
+  const float e = __fmaf_rn(-b.lo, r0, __fsub_rn(__fsub_rn(1.0f, p.hi), p.lo));
+  return quick_two_sum(r0, __fmul_rn(r0, e));
+}
+
 __device__ __forceinline__ dd dd_ldexp(dd a, int e) { return {ldexpf(a.hi, e), ldexpf(a.lo, e)}; }
 
 __device__ __forceinline__ dd dd_from_double(double x) {

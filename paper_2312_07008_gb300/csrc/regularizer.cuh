@@ -38,7 +38,7 @@ __device__ __forceinline__ void regularize(dd delta, dd s, const RegTables& R, d
   }
   if (x.hi > 40.0f) {
     *y = dd_make(0.0f);
-    *r1 = dd_div(dd_make(1.0f), delta);
+    *r1 = dd_recip(delta);
     return;
   }
   const dd t = dd_mul(x, R.log2e);
@@ -58,7 +58,7 @@ __device__ __forceinline__ void regularize(dd delta, dd s, const RegTables& R, d
   dd omy;
   if (q == 0) omy = dd_add_fast(R.C[j], dd_sub_fast(omp, dd_mul(R.C[j], omp)));
   else omy = dd_sub_fast(dd_make(1.0f), *y);
-  *r1 = dd_div(omy, delta);
+  *r1 = dd_mul(omy, dd_recip(delta));
 }
 
 
