@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+import bench  # noqa: E402
 import paper_2312_07008_gb300 as pkg  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,5 +75,7 @@ def test_workload_matches_stored_oracle(path, precision):
     for c in cuts:
         k, de, ef = got["cuts"][c]
         r = ref["cuts"][str(c)] if str(c) in ref["cuts"] else ref["cuts"][repr(c)]
+        # how far the cut was from moving (cumulative-fraction margins, widening stop gap)
+        print(ref["workload"], precision, bench.cut_margins(got["ons"], c, k))
         assert k == r["nkept"], (c, k, r["nkept"])
         assert abs(de - r["de"]) <= e_tol, (c, de, r["de"])
