@@ -217,8 +217,9 @@ int dsrg_fno_truncate_noalloc(int32_t nvir, const double* dvv, int32_t mode, dou
  *   C_out      device [npairs][nv][nv].
  * The 4-index integrals are formed for 16 values of a at a time and never
  * stored whole.  Errors: DSRG_FNO_ERR_ARG for bad sizes, null or host
- * pointers; sizes with nv^3 * 16 or npairs * nv^2 >= 2^31 and other
- * precisions give DSRG_FNO_ERR_UNSUPPORTED. */
+ * pointers; DSRG_FNO_ERR_NONFINITE for a NaN/Inf in B_vv or T; sizes with
+ * nv^3 * 16 or npairs * nv^2 >= 2^31 and other precisions give
+ * DSRG_FNO_ERR_UNSUPPORTED. */
 int dsrg_fno_ladder(int32_t nv, int32_t naux, const double* B_vv, int32_t npairs, const double* T,
                     int32_t precision, double* C_out, void* stream);
 
@@ -239,8 +240,9 @@ int dsrg_fno_ladder(int32_t nv, int32_t naux, const double* B_vv, int32_t npairs
  *              slices receive B' (the rest is left untouched).
  *   w_out      device [naux] or NULL: every eigenvalue of W, descending.
  *   naux_out   host: naux'.
- * Errors: DSRG_FNO_ERR_ARG for bad sizes, null or host pointers; other
- * precisions give DSRG_FNO_ERR_UNSUPPORTED. */
+ * Errors: DSRG_FNO_ERR_ARG for bad sizes, null or host pointers;
+ * DSRG_FNO_ERR_NONFINITE for a NaN/Inf in B_hp; other precisions give
+ * DSRG_FNO_ERR_UNSUPPORTED. */
 int dsrg_fno_naf(int32_t nh, int32_t np, int32_t naux, const double* B_hp, double threshold,
                  int32_t precision, double* B_out, double* w_out, int32_t* naux_out, void* stream);
 

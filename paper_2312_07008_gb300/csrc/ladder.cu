@@ -50,7 +50,18 @@ int impl_ladder(Workspace& ws, int32_t nv, int32_t naux, const double* Bvv, int3
             ws_bytes((size_t)ks * npairs * vpad, 2) + ws_bytes((size_t)ks * blk * vpad, 2) +
             ws_bytes(nv2, sizeof(int)) + ws_bytes(blk, sizeof(int)) + ws_bytes(npairs, sizeof(int)) +
             ws_bytes(blk + 16, sizeof(int));
+  need += ws_bytes(8, sizeof(int));
   DSRG_TRY(ws_reserve(ws, need));
+  {
+    int* flag = ws_take<int>(ws, 8);
+    int h = 0;
+    DSRG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    DSRG_TRY(check_finite(Bvv, (long)naux * nv2, flag, st));
+    DSRG_TRY(check_finite(T, (long)npairs * nv2, flag, st));
+    DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSRG_CUDA(cudaStreamSynchronize(st));
+    if (h) return DSRG_FNO_ERR_NONFINITE;
+  }
   double* I1 = ws_take<double>(ws, (size_t)blk * nv2);
   double* I2 = ws_take<double>(ws, (size_t)blk * nv2);
   int* err = ws_take<int>(ws, 16);

@@ -37,8 +37,18 @@ int impl_naf(Workspace& ws, int32_t nh, int32_t np, int32_t naux, const double* 
     planes = std::max(p1, p2);
   }
   const size_t need = 3 * ws_bytes(n2, sizeof(double)) + ws_bytes(eig_work_doubles(naux), sizeof(double)) +
-                      ws_bytes(naux + 16, sizeof(double)) + ws_bytes(naux + 16, sizeof(int)) + planes;
+                      ws_bytes(naux + 16, sizeof(double)) + ws_bytes(naux + 16, sizeof(int)) + planes +
+                      ws_bytes(8, sizeof(int));
   DSRG_TRY(ws_reserve(ws, need));
+  {
+    int* flag = ws_take<int>(ws, 8);
+    int h = 0;
+    DSRG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    DSRG_TRY(check_finite(B, (long)naux * L, flag, st));
+    DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSRG_CUDA(cudaStreamSynchronize(st));
+    if (h) return DSRG_FNO_ERR_NONFINITE;
+  }
   double* W = ws_take<double>(ws, n2);
   double* V = ws_take<double>(ws, n2);
   double* U = ws_take<double>(ws, n2);

@@ -46,6 +46,7 @@ constexpr int KCHUNK_BLOCKS = 320 / BKE;  // 320 k-values per exact sum of level
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s of clock cycles
 
 enum { MODE_PAIR = 0, MODE_SYRK = 1, MODE_PLAIN = 2 };
+constexpr int PLAIN_BAND = 8;  // row tiles per band of the plain mode's job order
 
 // ---------------------------------------------------------------- staging
 // Row exponent e with max |v| < 2^e (frexp exponent of the row maximum).
@@ -297,9 +298,23 @@ __device__ __forceinline__ bool decode_job(const GemmParams& P, int job, int* sl
     return true;
   }
   if (P.mode == MODE_PLAIN) {
+    // bands of PLAIN_BAND row tiles, column tile by column tile inside a
+    // band: the CTAs running at one time share their A tiles and each B tile
+    // is read once per band instead of once per row tile
     *slot = 0;
-    *mt = job / P.ntn;
-    *nt = job % P.ntn;
+    const int full = P.ntm / PLAIN_BAND;
+    const int per = PLAIN_BAND * P.ntn;
+    const int b = job / per;
+    if (b < full) {
+      const int r = job - b * per;
+      *nt = r / PLAIN_BAND;
+      *mt = b * PLAIN_BAND + r % PLAIN_BAND;
+    } else {
+      const int left = P.ntm - full * PLAIN_BAND;
+      const int r = job - full * per;
+      *nt = r / left;
+      *mt = full * PLAIN_BAND + r % left;
+    }
     return true;
   }
   // syrk: upper tiles only (some f >= e inside), all splits

@@ -34,3 +34,12 @@ def test_ladder_matches_oracle(prec, nv, naux, npairs):
     err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
     print(f"nv {nv} naux {naux} pairs {npairs} prec {prec}: max rel err {err:.2e}")
     assert err <= (1e-12 if prec == pkg.FP64 else 1e-10)
+
+
+def test_ladder_rejects_non_finite_input():
+    Bv, T = inputs(12, 20, 3, seed=5)
+    T[1, 2, 3] = np.inf
+    C = torch.empty((3, 12, 12), dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.DsrgFnoError) as ei:
+        pkg.dsrg_fno_ladder(torch.from_numpy(Bv).cuda(), torch.from_numpy(T).cuda(), C)
+    assert ei.value.status == -6

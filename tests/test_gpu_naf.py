@@ -81,3 +81,13 @@ def test_naf_rejects_host_arrays():
     st = pkg.load().dsrg_fno_naf(2, 20, p.naux, ctypes.c_void_p(p.B.ctypes.data), 0.0, pkg.SLICED_BF16,
                                  ctypes.c_void_p(Bo.data_ptr()), None, ctypes.byref(k), None)
     assert st == -1 and k.value == -9
+
+
+def test_naf_rejects_non_finite_factors():
+    p = make_problem(ncore=2, nact=1, nvir=20, naux=30, seed=94, nstates=2)
+    B = torch.from_numpy(np.ascontiguousarray(p.B)).cuda()
+    B[3, 1, 7] = float("nan")
+    Bo = torch.zeros_like(B)
+    with pytest.raises(pkg.DsrgFnoError) as ei:
+        pkg.dsrg_fno_naf(3, 21, p.naux, B, 0.0, pkg.SLICED_BF16, Bo)
+    assert ei.value.status == -6
