@@ -784,10 +784,10 @@ def naf_timing(pkg, dev, nslices, keep_frac=0.75):
 TRAFFIC = {
     "sa_cas10_ncore60_nvir1200_naux3600": {
         # small-case capture (energy pass of ncore 20 / nact 4 / nvir 1100 / naux 2000):
-        # 8.168 GB read + 2.912 GB written for 2.2556e13 executed flops
-        "bytes_per_exec_flop": (8.167924e9 + 2.912241e9) / 2.2556379709440e13,
+        # 9.282 GB read + 2.909 GB written for 2.2556e13 executed flops
+        "bytes_per_exec_flop": (9.281997e9 + 2.909286e9) / 2.2556379709440e13,
         "sha256": {"paper_2312_07008_gb300/csrc/sliced.cu":
-                   "19fb335de6ba7b82ebc631a5a7c45bd2a1e3d52c841a0eaab8fb2e083e73c9c6",
+                   "b89884bbd311d17a7e96e2810a17ce7c2913b6e9a847fc443f1a49302f0d9336",
                    "paper_2312_07008_gb300/csrc/tc_ptx.cuh":
                    "300804d055c2a37a13d0d68e3e9d556e62027073a7a31151f5033bd4885f0757"},
     },

@@ -733,7 +733,12 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   if (smem > (size_t)SMEM_CEILING) return DSRG_FNO_ERR_UNSUPPORTED;
   // one fixed ceiling for every launch: concurrent callers (batch workers)
   // never lower it under one another
-  if (!in_smem && g_eig_colpair.load()) return eig_colpair(n, m, A, V, work, status_dev, max_sweeps, st);
+  // (the column-pair kernel stages two columns of n per pair: above n of
+  // about 7000 it does not fit, and the round-parallel kernel takes the matrix)
+  if (!in_smem && g_eig_colpair.load()) {
+    const int rc = eig_colpair(n, m, A, V, work, status_dev, max_sweeps, st);
+    if (rc != DSRG_FNO_ERR_UNSUPPORTED) return rc;
+  }
   auto kern = in_smem ? jacobi_coop_kernel<true> : jacobi_coop_kernel<false>;
   if (smem > 48 * 1024)
     DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CEILING));
@@ -755,8 +760,13 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   int nblk = (int)std::min<long>(std::min(sms * std::min(occ, JACOBI_BLOCKS_PER_SM), JMAX_BLOCKS),
                                  (units + per_block - 1) / per_block);
   nblk = in_smem ? 1 : std::max(nblk, 1);
-  void* args[] = {&P};
-  DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(JNT), args, smem, st));
+  if (nblk == 1) {
+    // one block: its barrier is __syncthreads, no co-residency to guarantee
+    kern<<<1, JNT, smem, st>>>(P);
+  } else {
+    void* args[] = {&P};
+    DSRG_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(nblk), dim3(JNT), args, smem, st));
+  }
   DSRG_LAUNCH_CHECK();
   int h[3] = {0, 0, 0};
   DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
