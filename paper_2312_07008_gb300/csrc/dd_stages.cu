@@ -115,7 +115,7 @@ __device__ __forceinline__ dd dd_fma_acc(dd acc, dd c, dd s) {
 
 // Double-float form of the group dressing (same structure as dress.cu).
 template <int OCT>
-__global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const DressDesc* __restrict__ desc,
+__global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3) dress_dd_kernel(int nv, int na, const DressDesc* __restrict__ desc,
                                                        DressAux aux, const float2* __restrict__ tau,
                                                        const float2* __restrict__ kap, float2* __restrict__ sig,
                                                        double* __restrict__ sig_sign, double* __restrict__ e_part,
@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
   } cf;
   __shared__ double lam[OCT], sgn[OCT], dg[NS];
   __shared__ dd lamw[OCT], sqd[OCT];
-  __shared__ float2 tT[GT][GT + 1], tK[GT][GT + 1], sA[GT][GT + 1];
+  __shared__ float sgnf[OCT], dgf[NS];  // float copies: no float64 op in the loops
+  // transposed tiles double-buffered: one barrier per slot
+  __shared__ float2 tT[2][GT][GT + 1], tK[2][GT][GT + 1], sA[GT][GT + 1];
   __shared__ double red[GNT / 32];
   const DressDesc D = desc[blockIdx.y];
   group_coefficients<OCT>(D, aux, na, cf.d, lam, sgn, dg);
@@ -141,20 +143,51 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
   for (int o = threadIdx.x; o < oc; o += blockDim.x) {
     lamw[o] = dd_from_double(0.5 * lam[o]);
     sqd[o] = dd_from_double(sqrt(fabs(lam[o])));
+    sgnf[o] = sgn[o] > 0.0 ? 1.0f : -1.0f;
   }
+  for (int u = threadIdx.x; u < D.nslots; u += blockDim.x) dgf[u] = (float)dg[u];
   __syncthreads();
   const int ntd = (nv + GT - 1) / GT;
   const int nup = ntd * (ntd + 1) / 2;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const long nv2 = (long)nv * nv;
-  dd part = dd_make(0.0f);
-  for (int t = blockIdx.x; t < nup; t += gridDim.x) {
-    int rem = t, te = 0;
-    while (rem >= ntd - te) {
-      rem -= ntd - te;
-      ++te;
+  const int ns = D.nslots;
+  // upper tile t -> (te, tf), te <= tf; t only grows, so the row search
+  // resumes where the last one ended (row_te starts at tile row_base)
+  int row_te = 0, row_base = 0;
+  auto decode = [&](int t, int* te_, int* tf_) {
+    while (t >= row_base + (ntd - row_te)) {
+      row_base += ntd - row_te;
+      ++row_te;
     }
-    const int tf = te + rem;
+    *te_ = row_te;
+    *tf_ = row_te + (t - row_base);
+  };
+  // this thread's operands of slot u in tile (te, tf): tau and kappa at (e, f)
+  // and at (f, e) (the latter staged transposed through shared memory)
+  float2 na_ = make_float2(0.f, 0.f), nb_ = na_, nt_ = na_, nk_ = na_;
+  auto fetch = [&](int te, int tf, int u) {
+    const float2* T = tau + (long)(D.slot + u) * nv2;
+    const float2* K = kap + (long)(D.slot + u) * nv2;
+    const int e = te * GT + ty, f = tf * GT + tx;
+    const bool in = e < nv && f < nv;
+    na_ = in ? T[(long)e * nv + f] : make_float2(0.f, 0.f);
+    nb_ = in ? K[(long)e * nv + f] : make_float2(0.f, 0.f);
+    const int fr = tf * GT + ty, ec = te * GT + tx;
+    const bool ok = fr < nv && ec < nv;
+    nt_ = ok ? T[(long)fr * nv + ec] : make_float2(0.f, 0.f);
+    nk_ = ok ? K[(long)fr * nv + ec] : make_float2(0.f, 0.f);
+  };
+  dd part = dd_make(0.0f);
+  int t = blockIdx.x, te = 0, tf = 0, buf = 0;
+  if (t < nup) {
+    decode(t, &te, &tf);
+    fetch(te, tf, 0);
+  }
+  while (t < nup) {
+    const int tn = t + gridDim.x;
+    int ten = 0, tfn = 0;
+    if (tn < nup) decode(tn, &ten, &tfn);
     const int E0 = te * GT, F0 = tf * GT;
     const int e = E0 + ty, f = F0 + tx;
     const bool inside = e < nv && f < nv;
@@ -165,34 +198,32 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
       at[o] = dd_make(0.0f);
       ak[o] = dd_make(0.0f);
     }
-    for (int u = 0; u < D.nslots; ++u) {
-      const float2* T = tau + (long)(D.slot + u) * nv2;
-      const float2* K = kap + (long)(D.slot + u) * nv2;
-      {
-        const int fr = F0 + ty, ec = E0 + tx;
-        const bool ok = fr < nv && ec < nv;
-        tT[ty][tx] = ok ? T[(long)fr * nv + ec] : make_float2(0.f, 0.f);
-        tK[ty][tx] = ok ? K[(long)fr * nv + ec] : make_float2(0.f, 0.f);
-      }
+    for (int u = 0; u < ns; ++u) {
+      tT[buf][ty][tx] = nt_;
+      tK[buf][ty][tx] = nk_;
+      const dd a = {na_.x, na_.y}, b = {nb_.x, nb_.y};
+      // the next slot's (or the next tile's first slot's) loads fly during
+      // this slot's arithmetic
+      if (u + 1 < ns) fetch(te, tf, u + 1);
+      else if (tn < nup) fetch(ten, tfn, 0);
       __syncthreads();
-      const dd a = inside ? ld(T, (long)e * nv + f) : dd_make(0.0f);
-      const dd b = inside ? ld(K, (long)e * nv + f) : dd_make(0.0f);
       // c T + c sgn dg T^T = c (T + sgn dg T^T) with sgn = +-1, dg in {0, 1}:
       // the two signed combinations are formed once per slot
-      const float du = (float)dg[u];
-      const dd att = {du * tT[tx][ty].x, du * tT[tx][ty].y}, btt = {du * tK[tx][ty].x, du * tK[tx][ty].y};
+      const float du = dgf[u];
+      const float2 xt = tT[buf][tx][ty], xk = tK[buf][tx][ty];
+      const dd att = {du * xt.x, du * xt.y}, btt = {du * xk.x, du * xk.y};
       const dd tp = dd_add_fast(a, att), tm = dd_sub_fast(a, att);
       const dd kp = dd_add_fast(b, btt), km = dd_sub_fast(b, btt);
 #pragma unroll
       for (int o = 0; o < OCT; ++o) {
         if (o < oc) {
           const dd c = cf.f[u][o];
-          const bool pos = sgn[o] > 0.0;
+          const bool pos = sgnf[o] > 0.0f;
           at[o] = dd_fma_acc(at[o], c, pos ? tp : tm);
           ak[o] = dd_fma_acc(ak[o], c, pos ? kp : km);
         }
       }
-      __syncthreads();
+      buf ^= 1;
     }
 #pragma unroll
     for (int o = 0; o < OCT; ++o) {
@@ -214,7 +245,7 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
             sA[ty][tx] = make_float2(v.hi, v.lo);
             __syncthreads();
             const int fr = F0 + ty, ec = E0 + tx;
-            const float sg = (float)sgn[o];
+            const float sg = sgnf[o];
             const bool ok = fr < nv && ec < nv;
             if (ok) S[(long)fr * nv + ec] = make_float2(sg * sA[tx][ty].x, sg * sA[tx][ty].y);
             if (rowmax) {
@@ -228,6 +259,9 @@ __global__ void __launch_bounds__(GNT) dress_dd_kernel(int nv, int na, const Dre
         }
       }
     }
+    t = tn;
+    te = ten;
+    tf = tfn;
   }
   double pd = dd_to_double(part);
   for (int o = 16; o > 0; o >>= 1) pd += __shfl_down_sync(0xffffffffu, pd, o);
