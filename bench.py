@@ -804,8 +804,8 @@ def naf_timing(pkg, dev, nslices, keep_frac=0.75):
 TRAFFIC = {
     "sa_cas10_ncore60_nvir1200_naux3600": {
         # small-case capture (energy pass of ncore 20 / nact 4 / nvir 1100 / naux 2000):
-        # 9.282 GB read + 2.909 GB written for 2.2556e13 executed flops
-        "bytes_per_exec_flop": (9.281997e9 + 2.909286e9) / 2.2556379709440e13,
+        # 9.328 GB read + 2.908 GB written for 2.2556e13 executed flops
+        "bytes_per_exec_flop": (9.328328e9 + 2.907642e9) / 2.2556379709440e13,
         "sha256": {"paper_2312_07008_gb300/csrc/sliced.cu":
                    "4ae42af7897f57e9271091737d32b7b3ac1c4d64dea612fe28a0ab301f83f347",
                    "paper_2312_07008_gb300/csrc/tc_ptx.cuh":

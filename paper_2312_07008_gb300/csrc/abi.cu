@@ -287,10 +287,13 @@ static int run_pass(const Geometry& g, const double* B, const double* eps, const
     DSRG_PHASE("phase_density_eigen", st);
     const int ns = na * (na + 1) / 2, nd = na * (na - 1) / 2;
     DSRG_CUDA(cudaMemcpyAsync(W.g1A, gamma1, sizeof(double) * na * na, cudaMemcpyDeviceToDevice, st));
-    DSRG_TRY(eig_sym_jacobi(na, W.g1A, W.g1V, W.g1W, W.status, 60, st));
     DSRG_TRY(aa_blocks(na, gamma1, lambda2, W.MsA, W.MaA, st));
-    DSRG_TRY(eig_sym_jacobi(ns, W.MsA, W.MsV, W.MsW, W.status, 60, st));
-    if (nd > 0) DSRG_TRY(eig_sym_jacobi(nd, W.MaA, W.MaV, W.MaW, W.status, 60, st));
+    // Gamma1 and the two aa blocks of the hole 2-RDM, solved together
+    const int nn[3] = {na, ns, nd};
+    double* const AA[3] = {W.g1A, W.MsA, W.MaA};
+    double* const VV[3] = {W.g1V, W.MsV, W.MaV};
+    double* const WW[3] = {W.g1W, W.MsW, W.MaW};
+    DSRG_TRY(eig_sym_jacobi_batch(3, nn, AA, VV, WW, W.status, 60, st));
     aux.g1_evec = W.g1V;
     aux.g1_eval = W.g1A;
     aux.aas_evec = W.MsV;
@@ -415,7 +418,7 @@ static size_t pass_bytes(const Geometry& g, const Plan& P, bool want_d, int nspl
   b += 3 * doubles((size_t)na * na + 1) + doubles(eig_work_doubles(na));
   b += 2 * doubles((size_t)ns * ns + 1) + doubles(eig_work_doubles(ns));
   b += 2 * doubles((size_t)nd * nd + 1) + doubles(eig_work_doubles(nd));
-  b += ws_bytes(8, sizeof(int));
+  b += ws_bytes(16, sizeof(int));
   if (ks) {
     const size_t rows = (size_t)g.nh * g.np;
     b += ws_bytes((size_t)ks * rows * pad64(g.nq), 2) + ws_bytes(rows, sizeof(int));
@@ -458,7 +461,7 @@ static int carve_pass(Workspace& ws, const Geometry& g, const Plan& P, bool want
   W.MaA = ws_take<double>(ws, (size_t)nd * nd + 1);
   W.MaV = ws_take<double>(ws, (size_t)nd * nd + 1);
   W.MaW = ws_take<double>(ws, eig_work_doubles(nd));
-  W.status = ws_take<int>(ws, 8);
+  W.status = ws_take<int>(ws, 16);  // 4 per density eigensolve
   W.nsplit = nsplit;
   if (!W.status) return DSRG_FNO_ERR_NOMEM;
   W.ks = ks;

@@ -179,6 +179,10 @@ __global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3) dress_dd_kernel(int n
     nk_ = ok ? K[(long)fr * nv + ec] : make_float2(0.f, 0.f);
   };
   dd part = dd_make(0.0f);
+  // OCT = 2 (core pairs): sum_o lambda_o <sigma_o[tau], sigma_o[kappa]> is
+  // accumulated per output and weighted once at the end (two outputs' sums
+  // fit in registers; with 8 outputs they would lower the occupancy)
+  dd eacc[2] = {dd_make(0.0f), dd_make(0.0f)};
   int t = blockIdx.x, te = 0, tf = 0, buf = 0;
   if (t < nup) {
     decode(t, &te, &tf);
@@ -228,7 +232,12 @@ __global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3) dress_dd_kernel(int n
 #pragma unroll
     for (int o = 0; o < OCT; ++o) {
       if (o < oc) {
-        if (inside) part = dd_add(part, dd_mul_f(dd_mul(lamw[o], dd_mul(at[o], ak[o])), w));
+        if constexpr (OCT == 2) {
+          // w = 1 or 2: the scaling of at is exact
+          if (inside) eacc[o] = dd_fma_acc(eacc[o], dd{at[o].hi * w, at[o].lo * w}, ak[o]);
+        } else {
+          if (inside) part = dd_add(part, dd_mul_f(dd_mul(lamw[o], dd_mul(at[o], ak[o])), w));
+        }
         if (want_sig) {
           const dd v = dd_mul(sqd[o], at[o]);
           const long mat = D.out + D.o_begin + o;
@@ -262,6 +271,11 @@ __global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3) dress_dd_kernel(int n
     t = tn;
     te = ten;
     tf = tfn;
+  }
+  if constexpr (OCT == 2) {
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+      if (o < oc) part = dd_add(part, dd_mul(lamw[o], eacc[o]));
   }
   double pd = dd_to_double(part);
   for (int o = 16; o > 0; o >>= 1) pd += __shfl_down_sync(0xffffffffu, pd, o);

@@ -153,13 +153,29 @@ __device__ __forceinline__ dd dd_rsqrt12(dd x) {
   return y;
 }
 
+// The shared-memory solve (SM) is block-local: one block per matrix (a grid
+// may solve several), its barrier the block barrier.
+template <bool SM>
+__device__ __forceinline__ int jb_index() { return SM ? 0 : (int)blockIdx.x; }
+template <bool SM>
+__device__ __forceinline__ int jb_count() { return SM ? 1 : (int)gridDim.x; }
+template <bool SM>
+__device__ __forceinline__ bool jb_barrier(const JacobiArgs& P) {
+  if (SM) {
+    __syncthreads();
+    return true;
+  }
+  return grid_barrier(P);
+}
+
 // squared off-diagonal and total Frobenius norms of A (fixed summation order)
 template <bool SM>
 __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double* tot) {
   __shared__ double s_o[JNT], s_t[JNT];
   double o = 0.0, t = 0.0;
   const int n2 = P.n * P.n;
-  for (int idx = blockIdx.x * JNT + threadIdx.x; idx < n2; idx += gridDim.x * JNT) {
+  const int bi = jb_index<SM>(), nb = jb_count<SM>();
+  for (int idx = bi * JNT + threadIdx.x; idx < n2; idx += nb * JNT) {
     const float2 v = ldx2<SM>(A, idx);
     const double a = (double)v.x + (double)v.y;
     t += a * a;
@@ -175,16 +191,22 @@ __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double*
     }
     __syncthreads();
   }
+  if (SM) {
+    *off = s_o[0];
+    *tot = s_t[0];
+    __syncthreads();  // s_o, s_t are reused by the next call
+    return;
+  }
   if (threadIdx.x == 0) {
-    __stcg(P.red + 2 * blockIdx.x, s_o[0]);
-    __stcg(P.red + 2 * blockIdx.x + 1, s_t[0]);
+    __stcg(P.red + 2 * bi, s_o[0]);
+    __stcg(P.red + 2 * bi + 1, s_t[0]);
   }
   if (!grid_barrier(P)) {
     *off = -1.0;
     return;
   }
   double so = 0.0, st = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) {
+  for (int b = 0; b < nb; ++b) {
     so += __ldcg(P.red + 2 * b);
     st += __ldcg(P.red + 2 * b + 1);
   }
@@ -193,7 +215,8 @@ __device__ void norms(const JacobiArgs& P, const float2* A, double* off, double*
 }
 
 template <bool SM>
-__global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(JacobiArgs P) {
+__device__ void jacobi_solve(const JacobiArgs& P) {
+  const int bi = jb_index<SM>(), nb = jb_count<SM>();
   // per pair k of the round: c (hi, lo), s (hi, lo), then the pair (p < q);
   // with SM, then A, its ping-pong copy and V (n^2 float2 each)
   extern __shared__ float4 s_cs[];
@@ -203,12 +226,12 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
   float2* const A0 = SM ? reinterpret_cast<float2*>(s_cs + P.m) : P.A0;  // after s_pq (8 B x m/2 <= 16 B x m/2)
   float2* const A1 = SM ? A0 + n2 : P.A1;
   float2* const VV = SM ? A1 + n2 : P.V;
-  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+  for (long idx = bi * (long)JNT + threadIdx.x; idx < n2; idx += (long)nb * JNT) {
     const dd a = dd_from_double(P.A_in[idx]);
     stx<SM>(A0, (int)idx, a);
     stx<SM>(VV, (int)idx, dd_make(idx / n == idx % n ? 1.0f : 0.0f));
   }
-  if (!grid_barrier(P)) return;
+  if (!jb_barrier<SM>(P)) return;
   float2* A = A0;
   float2* B = A1;
   // rounding floor of a converged double-float sweep, relative and squared
@@ -259,9 +282,9 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
       float2* __restrict__ Bw = B;
       float2* __restrict__ Vw = VV;
       const int lane = threadIdx.x & 31;
-      const int nwarps = gridDim.x * (JNT / 32);
+      const int nwarps = nb * (JNT / 32);
 #pragma unroll 2
-      for (int task = blockIdx.x * (JNT / 32) + (threadIdx.x >> 5); task < ntasks; task += nwarps) {
+      for (int task = bi * (JNT / 32) + (threadIdx.x >> 5); task < ntasks; task += nwarps) {
         const int it = task / nchunks;
         const int k = (task - it * nchunks) * 32 + lane;
         if (k >= half) continue;
@@ -303,7 +326,7 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
           stx<SM>(Vw, i * n + qc, rot_combine(sR, v0, cR, v1, false));
         }
       }
-      if (!grid_barrier(P)) return;
+      if (!jb_barrier<SM>(P)) return;
       float2* tmp = A;
       A = B;
       B = tmp;
@@ -312,7 +335,7 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
   // Columns of V drift from unit length by rounding of the rotations; with
   // V = Vn N (N the column norms) the Rayleigh quotients become a_jj / N_j^2.
   double* nrm2 = reinterpret_cast<double*>(B);  // the free ping-pong buffer (n^2 >= n doubles)
-  for (int j = blockIdx.x * JNT + threadIdx.x; j < n; j += gridDim.x * JNT) {
+  for (int j = bi * JNT + threadIdx.x; j < n; j += nb * JNT) {
     dd acc = dd_make(0.0f);
     for (int i = 0; i < n; ++i) {
       const dd v = ldx<SM>(VV, i * n + j);
@@ -321,8 +344,8 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
     if (SM) nrm2[j] = dd_to_double(acc);
     else __stcg(nrm2 + j, dd_to_double(acc));
   }
-  if (!grid_barrier(P)) return;
-  for (long idx = blockIdx.x * (long)JNT + threadIdx.x; idx < n2; idx += (long)gridDim.x * JNT) {
+  if (!jb_barrier<SM>(P)) return;
+  for (long idx = bi * (long)JNT + threadIdx.x; idx < n2; idx += (long)nb * JNT) {
     const int i = (int)(idx / n), j = (int)(idx % n);
     const float2 a = ldx2<SM>(A, idx), v = ldx2<SM>(VV, idx);
     const double nj = SM ? nrm2[j] : __ldcg(nrm2 + j);
@@ -330,10 +353,24 @@ __global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(
     P.A_out[idx] = ((double)a.x + (double)a.y) / (i == j ? nj : sqrt(nj * ni));
     P.V_out[idx] = ((double)v.x + (double)v.y) / sqrt(nj);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bi == 0 && threadIdx.x == 0) {
     P.status[0] = converged ? 0 : 1;
     P.status[2] = sweeps_done;
   }
+}
+
+template <bool SM>
+__global__ void __launch_bounds__(JNT, JACOBI_BLOCKS_PER_SM) jacobi_coop_kernel(JacobiArgs P) {
+  jacobi_solve<SM>(P);
+}
+
+// several small matrices in shared memory, one block each
+constexpr int JBATCH_MAX = 4;
+struct JacobiBatch {
+  JacobiArgs a[JBATCH_MAX];
+};
+__global__ void __launch_bounds__(JNT, 1) jacobi_smem_batch_kernel(const __grid_constant__ JacobiBatch B) {
+  jacobi_solve<true>(B.a[blockIdx.x]);
 }
 
 
@@ -731,8 +768,6 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   const size_t smem = in_smem ? sizeof(float4) * (size_t)m + 3 * sizeof(float2) * (size_t)n * n
                               : (sizeof(float4) + sizeof(int2)) * (size_t)(m / 2);
   if (smem > (size_t)SMEM_CEILING) return DSRG_FNO_ERR_UNSUPPORTED;
-  // one fixed ceiling for every launch: concurrent callers (batch workers)
-  // never lower it under one another
   // (the column-pair kernel stages two columns of n per pair: above n of
   // about 7000 it does not fit, and the round-parallel kernel takes the matrix)
   if (!in_smem && g_eig_colpair.load()) {
@@ -740,6 +775,8 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
     if (rc != DSRG_FNO_ERR_UNSUPPORTED) return rc;
   }
   auto kern = in_smem ? jacobi_coop_kernel<true> : jacobi_coop_kernel<false>;
+  // one fixed ceiling for every launch: concurrent callers (batch workers)
+  // never lower it under one another
   if (smem > 48 * 1024)
     DSRG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CEILING));
   int dev = 0, sms = 0, occ = 0;
@@ -774,6 +811,54 @@ int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, i
   prof_count(n >= 256 ? "eig_sweeps_large" : "eig_sweeps_small", (double)h[2]);
   if (h[1]) return DSRG_FNO_ERR_TIMEOUT;
   return h[0] ? DSRG_FNO_ERR_NOCONV : DSRG_FNO_OK;
+}
+
+int eig_sym_jacobi_batch(int count, const int* n, double* const* A, double* const* V, double* const* work,
+                         int* status_dev, int max_sweeps, cudaStream_t st) {
+  if (count <= 0) return DSRG_FNO_OK;
+  if (count > JBATCH_MAX) return DSRG_FNO_ERR_ARG;
+  // matrices above the shared-memory size: one solve each, as eig_sym_jacobi
+  for (int e = 0; e < count; ++e)
+    if (n[e] > SMEM_JACOBI_N) DSRG_TRY(eig_sym_jacobi(n[e], A[e], V[e], work[e], status_dev + 4 * e, max_sweeps, st));
+  JacobiBatch Bt{};
+  int idx[JBATCH_MAX];
+  int k = 0;
+  size_t smem = 0;
+  for (int e = 0; e < count; ++e) {
+    if (n[e] <= 0 || n[e] > SMEM_JACOBI_N) continue;
+    const int m = (n[e] % 2 == 0) ? n[e] : n[e] + 1;
+    const long n2 = (long)n[e] * n[e];
+    JacobiArgs& P = Bt.a[k];
+    P.n = n[e];
+    P.m = m;
+    P.A_in = A[e];
+    P.A_out = A[e];
+    P.V_out = V[e];
+    P.A0 = P.A1 = P.V = nullptr;  // in shared memory
+    P.red = work[e] + 3 * n2;
+    P.bar = reinterpret_cast<unsigned*>(work[e] + 3 * n2 + 2 * JMAX_BLOCKS);
+    P.status = status_dev + 4 * e;
+    P.max_sweeps = max_sweeps;
+    smem = std::max(smem, sizeof(float4) * (size_t)m + 3 * sizeof(float2) * (size_t)n2);
+    DSRG_CUDA(cudaMemsetAsync(P.status, 0, 4 * sizeof(int), st));
+    idx[k++] = e;
+  }
+  if (k == 0) return DSRG_FNO_OK;
+  if (smem > 48 * 1024)
+    DSRG_CUDA(cudaFuncSetAttribute(jacobi_smem_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+  jacobi_smem_batch_kernel<<<k, JNT, smem, st>>>(Bt);
+  DSRG_LAUNCH_CHECK();
+  int h[4 * JBATCH_MAX];
+  DSRG_CUDA(cudaMemcpyAsync(h, status_dev, 4 * count * sizeof(int), cudaMemcpyDeviceToHost, st));
+  DSRG_CUDA(cudaStreamSynchronize(st));
+  int rc = DSRG_FNO_OK;
+  for (int q = 0; q < k; ++q) {
+    const int e = idx[q];
+    prof_count("eig_sweeps_small", (double)h[4 * e + 2]);
+    if (h[4 * e]) rc = DSRG_FNO_ERR_NOCONV;
+  }
+  return rc;
 }
 
 // evals/evecs sorted (descending or ascending) from the Jacobi output;

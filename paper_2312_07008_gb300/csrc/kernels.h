@@ -75,6 +75,10 @@ int eig_set_barrier_limit(long long spins);
 void set_eig_colpair(bool on);
 int eig_sym_jacobi(int n, double* A, double* V, double* work, int* status_dev, int max_sweeps,
                    cudaStream_t st);
+// eig_sym_jacobi on up to 4 matrices at once: those with n <= 80 in one
+// launch, one block each; status_dev: 4 ints per matrix.
+int eig_sym_jacobi_batch(int count, const int* n, double* const* A, double* const* V, double* const* work,
+                         int* status_dev, int max_sweeps, cudaStream_t st);
 // Marks the calling thread, for the scope's lifetime, as one of several host
 // threads that share the device (batch workers): the eigensolver then keeps
 // its cooperative grid small, since its blocks stay resident through every
