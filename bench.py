@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the sub-results (CAS(12,12) workload and the 64-instance batch)")
+    ap.add_argument("--clock-ms", type=int, default=200,
+                    help="nvidia-smi sampling interval during the timed steps (ms)")
     ap.add_argument("--fused-epilogue", action="store_true",
                     help="run the Eq. A7 regulariser in the contraction kernel (comparison with the separate default)")
     return ap.parse_args()
@@ -123,8 +125,9 @@ def measured_peaks():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, interval_ms: int = 200):
         self.dev = device_index
+        self.interval = max(int(interval_ms), 50)
         self.lines = []
         self.proc = None
 
@@ -134,7 +137,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                          "-i", str(self.dev), "-lms", str(self.interval)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except OSError:
@@ -506,7 +509,7 @@ def main():
         step(gp)
     stream = torch.cuda.current_stream()
     barrier()
-    clk = ClockSampler(local)
+    clk = ClockSampler(local, args.clock_ms)
     clk.start()
     time.sleep(0.3)
     pkg.dsrg_fno_launch_count(reset=True)
@@ -905,7 +908,7 @@ def batch_arm(args):
     workers = pkg.dsrg_fno_batch_last_workers()
     stream = torch.cuda.current_stream()
     barrier()
-    clk = ClockSampler(local)
+    clk = ClockSampler(local, args.clock_ms)
     clk.start()
     time.sleep(0.3)
     # timed steps without the profiling hooks: eight workers recording events
