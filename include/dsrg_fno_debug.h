@@ -83,6 +83,14 @@ int dsrg_fno_debug_set_syrk_planes(int32_t nslices);
  * global memory (for comparison).  Affects later calls of this process. */
 int dsrg_fno_debug_set_eig_colpair(int32_t on);
 
+/* Symmetric eigensolves of `count` (1..4) matrices at once, as the density
+ * step of every pass does: n[e] x n[e] row-major float64 matrices A[e] (host,
+ * overwritten: eigenvalues on the diagonal, unsorted), eigenvectors into the
+ * columns of V[e] (host, n[e] x n[e]).  Matrices up to 80 x 80 share one
+ * launch (one block each), larger ones are solved one after another first.
+ * Allocates device memory; DSRG_FNO_ERR_NOCONV if a solve did not converge. */
+int dsrg_fno_debug_eig_batch(int32_t count, const int32_t* n, double* const* A, double* const* V);
+
 /* Bytes of device workspace the single-instance calls hold on the current
  * device (grow-only; 0 before the first call and after dsrg_fno_release()).
  * Host only: reads the library's bookkeeping, launches nothing. */

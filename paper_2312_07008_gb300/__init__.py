@@ -9,7 +9,7 @@ from .binding import (  # noqa: F401
     dsrg_fno_truncate_noalloc, dsrg_fno_cut, dsrg_fno_naf, dsrg_fno_ladder,
     dsrg_fno_discarded_correction, dsrg_fno_sa_densities, dsrg_fno_batch_run, dsrg_fno_batch_last_workers,
     dsrg_fno_release, dsrg_fno_profile_enable, dsrg_fno_profile_query, dsrg_fno_launch_count,
-    dsrg_fno_debug_workspace_bytes, dsrg_fno_set_log_callback, dsrg_fno_debug_pair_tiles,
+    dsrg_fno_debug_workspace_bytes, dsrg_fno_debug_eig_batch, dsrg_fno_set_log_callback, dsrg_fno_debug_pair_tiles,
     dsrg_fno_debug_set_barrier_limit, dsrg_fno_debug_set_fused_epilogue, dsrg_fno_debug_set_syrk_planes, dsrg_fno_debug_set_eig_colpair,
     load, LIB_PATH, EXPORTED,
 )

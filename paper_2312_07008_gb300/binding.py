@@ -37,6 +37,7 @@ EXPORTED = (
     "dsrg_fno_debug_regularizer",
     "dsrg_fno_debug_mma_schedule",
     "dsrg_fno_debug_workspace_bytes",
+    "dsrg_fno_debug_eig_batch",
     "dsrg_fno_debug_pair_tiles",
     "dsrg_fno_debug_set_barrier_limit",
     "dsrg_fno_debug_set_fused_epilogue",
@@ -138,6 +139,9 @@ def load(path: str = LIB_PATH):
     lib.dsrg_fno_debug_set_fused_epilogue.restype = ctypes.c_int
     lib.dsrg_fno_debug_set_barrier_limit.argtypes = [ctypes.c_int64]
     lib.dsrg_fno_debug_set_barrier_limit.restype = ctypes.c_int
+    lib.dsrg_fno_debug_eig_batch.argtypes = [i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.POINTER(d)),
+                                             ctypes.POINTER(ctypes.POINTER(d))]
+    lib.dsrg_fno_debug_eig_batch.restype = ctypes.c_int
     lib.dsrg_fno_debug_workspace_bytes.argtypes = []
     lib.dsrg_fno_debug_workspace_bytes.restype = ctypes.c_int64
     lib.dsrg_fno_set_log_callback.argtypes = [LOG_FN, vp]
@@ -359,6 +363,20 @@ def dsrg_fno_debug_mma_schedule(nslices: int):
     n = load().dsrg_fno_debug_mma_schedule(int(nslices), buf, 64)
     _check("dsrg_fno_debug_mma_schedule", min(n, 0))
     return [tuple(buf[5 * i:5 * i + 5]) for i in range(n)]
+
+
+def dsrg_fno_debug_eig_batch(mats):
+    """Eigensolves of up to 4 symmetric float64 matrices in one call (the
+    density step's batched solve).  Returns [(A with eigenvalues on its
+    diagonal, V)] per matrix."""
+    n = len(mats)
+    outA = [np.ascontiguousarray(np.array(m, dtype=np.float64)) for m in mats]
+    outV = [np.zeros_like(a) for a in outA]
+    dims = (ctypes.c_int32 * n)(*[a.shape[0] for a in outA])
+    pa = (ctypes.POINTER(ctypes.c_double) * n)(*[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in outA])
+    pv = (ctypes.POINTER(ctypes.c_double) * n)(*[v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for v in outV])
+    _check("dsrg_fno_debug_eig_batch", load().dsrg_fno_debug_eig_batch(n, dims, pa, pv))
+    return list(zip(outA, outV))
 
 
 def dsrg_fno_debug_workspace_bytes() -> int:

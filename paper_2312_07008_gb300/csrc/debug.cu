@@ -111,6 +111,37 @@ extern "C" int dsrg_fno_debug_mma_schedule(int32_t ks, int32_t* entries, int32_t
   return n;
 }
 
+extern "C" int dsrg_fno_debug_eig_batch(int32_t count, const int32_t* n, double* const* A, double* const* V) {
+  if (count < 1 || count > 4 || !n || !A || !V) return DSRG_FNO_ERR_ARG;
+  for (int e = 0; e < count; ++e)
+    if (n[e] < 0 || n[e] > 4096 || (n[e] > 0 && (!A[e] || !V[e]))) return DSRG_FNO_ERR_ARG;
+  DevBuf dA[4], dV[4], dW[4], stat;
+  double *pa[4] = {}, *pv[4] = {}, *pw[4] = {};
+  int nn[4] = {};
+  for (int e = 0; e < count; ++e) {
+    nn[e] = n[e];
+    const size_t n2 = (size_t)n[e] * n[e];
+    DSRG_CUDA(cudaMalloc(&dA[e].p, sizeof(double) * (n2 + 1)));
+    DSRG_CUDA(cudaMalloc(&dV[e].p, sizeof(double) * (n2 + 1)));
+    DSRG_CUDA(cudaMalloc(&dW[e].p, sizeof(double) * eig_work_doubles(n[e])));
+    if (n2) DSRG_CUDA(cudaMemcpy(dA[e].p, A[e], sizeof(double) * n2, cudaMemcpyHostToDevice));
+    pa[e] = (double*)dA[e].p;
+    pv[e] = (double*)dV[e].p;
+    pw[e] = (double*)dW[e].p;
+  }
+  DSRG_CUDA(cudaMalloc(&stat.p, sizeof(int) * 16));
+  const int rc = eig_sym_jacobi_batch(count, nn, pa, pv, pw, (int*)stat.p, 60, 0);
+  DSRG_CUDA(cudaDeviceSynchronize());
+  if (rc != DSRG_FNO_OK) return rc;
+  for (int e = 0; e < count; ++e) {
+    const size_t n2 = (size_t)n[e] * n[e];
+    if (!n2) continue;
+    DSRG_CUDA(cudaMemcpy(A[e], pa[e], sizeof(double) * n2, cudaMemcpyDeviceToHost));
+    DSRG_CUDA(cudaMemcpy(V[e], pv[e], sizeof(double) * n2, cudaMemcpyDeviceToHost));
+  }
+  return DSRG_FNO_OK;
+}
+
 extern "C" int64_t dsrg_fno_debug_workspace_bytes(void) {
   std::lock_guard<std::mutex> lk(workspace_mutex());
   return (int64_t)workspace_for_current_device().cap;

@@ -145,3 +145,21 @@ def test_column_pairs_in_several_shared_memory_chunks(colpair):
         pkg.dsrg_fno_debug_set_eig_colpair(True)
     check(D, ons, nos, groups=False)
 
+
+
+def test_density_step_solves_several_matrices_in_one_call():
+    """The density step of a pass solves Gamma1 and the two aa blocks of the
+    hole 2-RDM together: matrices up to 80 x 80 share one launch, one block
+    each; a larger one (91 x 91, the symmetric aa block of 13 active
+    orbitals) is solved on its own first."""
+    rng = np.random.default_rng(5)
+    mats = []
+    for n in (10, 91, 55, 1):
+        X = rng.standard_normal((n, n))
+        mats.append(X + X.T)
+    out = pkg.dsrg_fno_debug_eig_batch(mats)
+    assert len(out) == len(mats)
+    for D, (A, V) in zip(mats, out):
+        lam = np.diag(A)
+        order = np.argsort(-lam, kind="stable")
+        check(D, lam[order], V[:, order])
