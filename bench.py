@@ -944,36 +944,55 @@ def batch_arm(args):
     value = replica_rate(args.steps * n, world, ms_max)
     flops = sum(algorithmic_flops(p) for p in probs)
 
-    # ---- end to end: every instance's inputs from pinned host memory each step
-    host, dbufs, gp_e2e = [], [], []
+    # ---- end to end: every instance's inputs from pinned host memory each
+    # step, into one of two device input sets on a copy stream: the copy of
+    # batch i + 1 runs while batch i computes (the batch call returns only
+    # when its instances are done, so the copy is issued just before it)
+    host = []
     for p in probs:
-        h = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
-             for k, v in (("B", p.B), ("eps", p.eps), ("g1", p.gamma1), ("l2", p.lambda2)) if v is not None}
-        db = {k: torch.empty_like(v, device=dev) for k, v in h.items()}
-        host.append(h)
-        dbufs.append(db)
-        gp_e2e.append(pkg.Problem(p.ncore, p.nact, p.nvir, p.naux, db["B"], db["eps"], db.get("g1"), db.get("l2"),
-                                  None, p.weights, p.s, pkg.SLICED_BF16, args.nslices))
+        host.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+                     for k, v in (("B", p.B), ("eps", p.eps), ("g1", p.gamma1), ("l2", p.lambda2))
+                     if v is not None})
+    sets, gsets = [], []
+    for _ in range(2):
+        dbufs = [{k: torch.empty_like(v, device=dev) for k, v in h.items()} for h in host]
+        sets.append(dbufs)
+        gsets.append([pkg.Problem(p.ncore, p.nact, p.nvir, p.naux, db["B"], db["eps"], db.get("g1"),
+                                  db.get("l2"), None, p.weights, p.s, pkg.SLICED_BF16, args.nslices)
+                      for p, db in zip(probs, dbufs)])
     h2d = sum(v.numel() * v.element_size() for h in host for v in h.values())
     on_host = [torch.empty(p.nvir, dtype=torch.float64).pin_memory() for p in probs]
     d2h = sum(x.numel() * 8 for x in on_host) + n * 8 * 3
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step():
-        for h, db in zip(host, dbufs):
-            for k in h:
-                db[k].copy_(h[k], non_blocking=True)
-        r = step(gp_e2e)
-        for a, b in zip(on_host, on):
-            a.copy_(b, non_blocking=True)
+    def issue_copy(j):
+        with torch.cuda.stream(copy_stream):
+            for h, db in zip(host, sets[j]):
+                for k in h:
+                    db[k].copy_(h[k], non_blocking=True)
+        copied[j].record(copy_stream)
+
+    def e2e_run(nsteps):
+        torch.cuda.synchronize()
+        issue_copy(0)
+        r = None
+        for i in range(nsteps):
+            j = i % 2
+            copied[j].synchronize()  # this batch's inputs are on the device
+            if i + 1 < nsteps:
+                issue_copy(1 - j)  # set 1 - j was last read by batch i - 1, which has returned
+            r = step(gsets[j])
+            for a, b in zip(on_host, on):
+                a.copy_(b, non_blocking=True)
         torch.cuda.synchronize()
         return r
 
-    e2e_step()
+    e2e_run(1)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    e2e_run(args.steps)
     e1.record(stream)
     barrier()
     e2e_value = replica_rate(args.steps * n, world, max_over_ranks(e0.elapsed_time(e1), dist, dev))
