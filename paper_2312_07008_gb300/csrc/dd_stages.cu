@@ -115,11 +115,11 @@ __device__ __forceinline__ dd dd_fma_acc(dd acc, dd c, dd s) {
 
 // Double-float form of the group dressing (same structure as dress.cu).
 template <int OCT>
-__global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3) dress_dd_kernel(int nv, int na, const DressDesc* __restrict__ desc,
-                                                       DressAux aux, const float2* __restrict__ tau,
-                                                       const float2* __restrict__ kap, float2* __restrict__ sig,
-                                                       double* __restrict__ sig_sign, double* __restrict__ e_part,
-                                                       int want_sig, unsigned* __restrict__ rowmax) {
+__global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3)
+    dress_dd_kernel(int nv, int na, const DressDesc* __restrict__ desc, DressAux aux,
+                    const float2* __restrict__ tau, const float2* __restrict__ kap, float2* __restrict__ sig,
+                    double* __restrict__ sig_sign, double* __restrict__ e_part, int want_sig,
+                    unsigned* __restrict__ rowmax) {
   constexpr int NS = (OCT == 2) ? 1 : MAXSLOT;
   // float64 coefficients, converted in place to double-float (same size)
   __shared__ union {
