@@ -611,6 +611,8 @@ def main():
         f64_alg = pair_alg_flops(p, [r64[c][0] for c in cuts]) * args.fp64_steps
         f64_tf = f64_alg / (f64_ms / 1e3) / 1e12 if f64_ms > 0 else None
         fp64 = {"solves_per_s": 1e3 / fms, "s_per_solve": fms / 1e3, "gflops": flops / (fms / 1e3) / 1e9,
+                "note": "contractions and elementwise stages in float64; the eigensolves run in double-float "
+                        "(about 48 bits) in both forms",
                 "roofline": {"bound": "fp64", "kernel": "pair_gemm_f64_kernel (float64 CUDA cores)",
                              "achieved": f64_tf, "unit": "TFLOP/s", "launches": f64_n,
                              "ms_per_step": f64_ms / args.fp64_steps,
