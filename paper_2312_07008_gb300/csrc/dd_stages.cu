@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3)
                     const float2* __restrict__ tau, const float2* __restrict__ kap, float2* __restrict__ sig,
                     double* __restrict__ sig_sign, double* __restrict__ e_part, int want_sig,
                     unsigned* __restrict__ rowmax) {
+  static_assert(OCT % 2 == 0, "coefficients are read two outputs at a time");
   constexpr int NS = (OCT == 2) ? 1 : MAXSLOT;
   // float64 coefficients, converted in place to double-float (same size)
-  __shared__ union {
+  __shared__ __align__(16) union {
     double d[NS][OCT];
     dd f[NS][OCT];
   } cf;
@@ -152,6 +153,10 @@ __global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3)
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const long nv2 = (long)nv * nv;
   const int ns = D.nslots;
+  unsigned posmask = 0;  // bit o: output o is symmetric (sgn +1)
+#pragma unroll
+  for (int o = 0; o < OCT; ++o)
+    if (o < oc && sgnf[o] > 0.0f) posmask |= 1u << o;
   // upper tile t -> (te, tf), te <= tf; t only grows, so the row search
   // resumes where the last one ended (row_te starts at tile row_base)
   int row_te = 0, row_base = 0;
@@ -218,13 +223,22 @@ __global__ void __launch_bounds__(GNT, (OCT == 2) ? 4 : 3)
       const dd att = {du * xt.x, du * xt.y}, btt = {du * xk.x, du * xk.y};
       const dd tp = dd_add_fast(a, att), tm = dd_sub_fast(a, att);
       const dd kp = dd_add_fast(b, btt), km = dd_sub_fast(b, btt);
+      // the slot's coefficients, two outputs per 16-byte shared load
+      const float4* cu = reinterpret_cast<const float4*>(&cf.f[u][0]);
 #pragma unroll
-      for (int o = 0; o < OCT; ++o) {
-        if (o < oc) {
-          const dd c = cf.f[u][o];
-          const bool pos = sgnf[o] > 0.0f;
-          at[o] = dd_fma_acc(at[o], c, pos ? tp : tm);
-          ak[o] = dd_fma_acc(ak[o], c, pos ? kp : km);
+      for (int o2 = 0; o2 < OCT; o2 += 2) {
+        if (o2 < oc) {
+          const float4 c2 = cu[o2 >> 1];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int o = o2 + h;
+            if (o < oc) {
+              const dd c = h ? dd{c2.z, c2.w} : dd{c2.x, c2.y};
+              const bool pos = (posmask >> o) & 1u;
+              at[o] = dd_fma_acc(at[o], c, pos ? tp : tm);
+              ak[o] = dd_fma_acc(ak[o], c, pos ? kp : km);
+            }
+          }
         }
       }
       buf ^= 1;
