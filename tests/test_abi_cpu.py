@@ -98,3 +98,21 @@ def test_log_callback_can_be_cleared():
     k = ctypes.c_int32()
     assert lib.dsrg_fno_truncate_noalloc(600, None, 0, 98.5, 0.01, None, None, ctypes.byref(k), None) == -1
     assert msgs == []
+
+
+def test_eig_batch_rejects_bad_arguments_before_any_work():
+    """The batched density eigensolve's test hook checks its arguments on the
+    host: 1 to 4 matrices, sizes in range and non-null arrays."""
+    import paper_2312_07008_gb300 as pkg
+    lib = pkg.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    a = (ctypes.c_double * 4)()
+    arr = (dp * 5)(*([ctypes.cast(a, dp)] * 5))
+    nul = (dp * 1)()
+    dims = lambda *n: (ctypes.c_int32 * len(n))(*n)  # noqa: E731
+    assert lib.dsrg_fno_debug_eig_batch(0, dims(2), arr, arr) == -1
+    assert lib.dsrg_fno_debug_eig_batch(5, dims(2, 2, 2, 2, 2), arr, arr) == -1
+    assert lib.dsrg_fno_debug_eig_batch(1, dims(-1), arr, arr) == -1
+    assert lib.dsrg_fno_debug_eig_batch(1, dims(5000), arr, arr) == -1
+    assert lib.dsrg_fno_debug_eig_batch(1, dims(2), nul, arr) == -1
+    assert lib.dsrg_fno_debug_eig_batch(1, None, arr, arr) == -1
