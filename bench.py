@@ -840,8 +840,8 @@ def traffic_per_launch(workload, exec_flops_per_launch):
     return t["bytes_per_exec_flop"] * exec_flops_per_launch
 
 
-# Peaks this repository measured itself (the driver measures bf16 and HBM
-# only): cuBLAS float64 and TF32 GEMMs through torch.matmul on one GB300,
+# Peaks this repository measured itself (MEASURED_PEAKS.json holds bf16 and
+# HBM only): cuBLAS float64 and TF32 GEMMs through torch.matmul on one GB300,
 # n = 8192, best of 5 or 10, CUDA events, SM clock at its 2070 MHz maximum.
 PEAKS_OWN = {"fp64_dgemm_tflops": 1.0988, "tf32_tflops": 1027.07}
 
