@@ -263,6 +263,123 @@ def e_vv(prob, components=None):
 
 
 # --------------------------------------------------------------------------
+# Full multi-reference SA-DSRG-PT2 energy (the scalar of Eq. A4's H-bar)
+# --------------------------------------------------------------------------
+def t2_general(prob):
+    """Dense first-order doubles t^{ij}_{ab} = <ab|ij> R(Delta^{ij}_{ab}) of
+    Eq. A7 for every hole pair (i, j in core + active) and particle pair
+    (a, b in active + virtual), zero on the all-active block, which the
+    cluster operator excludes.  Returns (t [nh][nh][np][np], nu, Delta)."""
+    sp = spaces(prob)
+    eh, ep = hole_eps(prob), particle_eps(prob)
+    nu = np.einsum("Qia,Qjb->ijab", prob.B, prob.B, optimize=True)
+    d = (eh[:, None, None, None] + eh[None, :, None, None]
+         - ep[None, None, :, None] - ep[None, None, None, :])
+    t = nu * regularizer(d, prob.s)
+    t[sp.nc:, sp.nc:, : sp.na, : sp.na] = 0.0
+    return t, nu, d
+
+
+def t1_general(prob, t2):
+    """First-order singles t^i_a of Eq. A6 for every hole i and particle a
+    (zero when both are active):
+        t^i_a = [f^i_a + r^i_a] R(Delta^i_a),
+        r^i_a = 1/2 sum_{ux} Delta^x_u Gamma^x_u tcheck^{iu}_{ax},
+    with tcheck^{iu}_{ax} = 2 t^{iu}_{ax} - t^{ui}_{ax} and Delta^x_u =
+    eps_x - eps_u.  r^i_a is the one-body part of [H0, T2] (the term Eq. A6
+    adds to f).  Returns (t1 [nh][np], f, r, Delta^i_a)."""
+    sp = spaces(prob)
+    eh, ep = hole_eps(prob), particle_eps(prob)
+    f = (np.zeros((sp.nh, sp.np_)) if prob.f_hp is None
+         else np.array(prob.f_hp, dtype=np.float64))
+    r = np.zeros_like(f)
+    if sp.na:
+        act = slice(sp.nc, sp.nh)
+        dxu = ep[: sp.na][None, :] - eh[act][:, None]            # [u][x] = eps_x - eps_u
+        tch = (2.0 * t2[:, act, :, : sp.na]
+               - np.transpose(t2[act, :, :, : sp.na], (1, 0, 2, 3)))   # [i][u][a][x]
+        r = 0.5 * np.einsum("ux,xu,iuax->ia", dxu, prob.gamma1, tch, optimize=True)
+    d1 = eh[:, None] - ep[None, :]
+    t1 = (f + r) * regularizer(d1, prob.s)
+    t1[sp.nc:, : sp.na] = 0.0
+    return t1, f, r, d1
+
+
+def commutator_scalar(prob, X1, X2, T1, T2, lambda3=None):
+    """<[X, T]>_0: the fully contracted part of the commutator of
+        X = sum_{ia} X1[i][a] E^i_a + 1/2 sum_{ijab} X2[i][j][a][b] E^{ij}_{ab}
+        T = sum_{kc} T1[k][c] E^c_k + 1/2 sum_{klcd} T2[k][l][c][d] E^{cd}_{kl}
+    (i, j, k, l holes; a, b, c, d particles; X2 and T2 symmetric under the
+    pair transpose), both normal ordered with respect to the ensemble in the
+    Mukherjee-Kutzelnigg sense named after Eq. A2.
+
+    The terms follow from the generalised Wick theorem: contractions between
+    the two strings are gamma = Gamma/2 (creator of X with annihilator of T),
+    eta = Theta/2 (annihilator of X with creator of T) and one density
+    cumulant; a term made of cumulants alone is the same in both orders and
+    cancels, so every term has at most one cumulant.  Spins are summed with
+    the spin-free cumulants defined after Eq. A12 (the alpha and beta
+    1-RDMs equal), which gives (Gamma over holes: 2 on the core diagonal;
+    Theta over particles: 2 on the virtual diagonal; cumulants on the active
+    indices only)
+      1/2 X1 T1 Gamma Theta
+      + 1/8 sum Gamma2_H[i][j][k][l] X2^{ij}_{ab} (Theta Theta T2)^{kl}_{ab}
+      + the one-cumulant terms written out below."""
+    sp = spaces(prob)
+    nc, na, nh = sp.nc, sp.na, sp.nh
+    G = gamma1_holes(prob)
+    G2 = gamma2_holes(prob)
+    Th = np.zeros((sp.np_, sp.np_))
+    Th[na:, na:] = 2.0 * np.eye(sp.nv)
+    if na:
+        Th[:na, :na] = theta(prob)
+    e = 0.5 * np.einsum("ia,kc,ik,ca->", X1, T1, G, Th, optimize=True)
+    tt = np.einsum("ac,bd,klcd->klab", Th, Th, T2, optimize=True)
+    e += 0.125 * np.einsum("ijkl,ijab,klab->", G2, X2, tt, optimize=True)
+    if na == 0:
+        return e
+    L = prob.lambda2
+    h, p = slice(nc, nh), slice(0, na)       # active holes, active particles
+    # one-body X with two-body T
+    e += 0.5 * np.einsum("ia,klcd,da,iclk->", X1[h], T2[h, h, p], Th, L, optimize=True)
+    e -= 0.5 * np.einsum("ia,klcd,ik,cdal->", X1[:, p], T2[:, h, p, p], G, L, optimize=True)
+    # two-body X with one-body T
+    e += 0.5 * np.einsum("ijab,kc,ca,ijkb->", X2[h, h, :, p], T1[h], Th, L, optimize=True)
+    e -= 0.5 * np.einsum("ijab,kc,jk,icab->", X2[h, :, p, p], T1[:, p], G, L, optimize=True)
+    # two-body X with two-body T, one 2-cumulant
+    e -= 0.25 * np.einsum("ijab,klcd,jk,da,iclb->", X2[h, :, :, p], T2[:, h, p], G, Th, L, optimize=True)
+    e -= 0.25 * np.einsum("ijab,klcd,jl,da,icbk->", X2[h, :, :, p], T2[h, :, p], G, Th, L, optimize=True)
+    e -= 0.25 * np.einsum("ijab,klcd,jk,db,ical->", X2[h, :, p], T2[:, h, p], G, Th, L, optimize=True)
+    e += 0.5 * np.einsum("ijab,klcd,jl,db,icak->", X2[h, :, p], T2[h, :, p], G, Th, L, optimize=True)
+    e += 0.125 * np.einsum("ijab,klcd,il,jk,cdba->", X2[:, :, p, p], T2[:, :, p, p], G, G, L, optimize=True)
+    if lambda3 is not None:
+        # one 3-cumulant Lambda^{xyz}_{uvw} = lambda3[x][y][z][u][v][w]
+        e += 0.5 * np.einsum("ijab,klcd,da,ijclbk->", X2[h, h, :, p], T2[h, h, p], Th, lambda3, optimize=True)
+        e -= 0.5 * np.einsum("ijab,klcd,jk,icdabl->", X2[h, :, p, p], T2[:, h, p, p], G, lambda3, optimize=True)
+    return e
+
+
+def pt2_energy(prob, lambda3=None):
+    """Second-order SA-DSRG energy E^(2) = <[H, A]>_0 + 1/2 <[[H0, A], A]>_0,
+    the correlation part of <H-bar^[2]> (Eq. A4), with A = T - T^+ and the
+    first-order T1, T2 of Eqs. A6, A7 over every class (core and active holes,
+    active and virtual particles).  `lambda3` adds the 3-cumulant terms; without
+    it they are dropped, which Sec. 2 allows when the 1-RDM drops them too.
+
+    With H Hermitian and [H0, T] an excitation operator, every scalar reduces to
+    2 <[X, T]>_0 with the de-excitation vertex X = H + 1/2 [H0, T]^+ restricted
+    to upper holes and lower particles:
+      X2^{ij}_{ab} = <ab|ij> - 1/2 Delta^{ij}_{ab} t^{ij}_{ab},
+      X1^i_a       = f^i_a - 1/2 Delta^i_a t^i_a + 1/2 r^i_a
+    (the all-active parts of X and of [H0, T] contract with nothing)."""
+    T2, nu, d2 = t2_general(prob)
+    T1, f, r, d1 = t1_general(prob, T2)
+    X2 = nu - 0.5 * d2 * T2
+    X1 = f - 0.5 * d1 * T1 + 0.5 * r
+    return 2.0 * commutator_scalar(prob, X1, X2, T1, T2, lambda3)
+
+
+# --------------------------------------------------------------------------
 # D_vv (Eq. A12, terms 1-12; the Lambda3 term 13 only with a 3-cumulant)
 # --------------------------------------------------------------------------
 def dvv_terms(prob, terms=range(1, 14), ts=None, t1=None, core_pairs=None, lambda3=None, ca_pairs=None,

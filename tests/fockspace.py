@@ -4,6 +4,8 @@ Evaluates, with explicit matrices over N-electron determinants, the
 definitions that Eq. A12 and the vv energy are derived from:
   Gamma^(2)_ef = 1/2 sum_a w_a <Psi_a| [[E_ef, A], A] |Psi_a>      (Eq. A11)
   E_vv         = sum_a w_a <Psi_a| [V, A_vv] + 1/2 [[H0, A_vv], A_vv] |Psi_a>  (Eq. A4)
+  E^(2)        = sum_a w_a <Psi_a| [H, A] + 1/2 [[H0, A], A] |Psi_a>  (every class,
+                 the Hamiltonian's every block; `hamiltonian`, `energy`)
 with A = T - T^+, the cluster operators normal ordered (Mukherjee-Kutzelnigg)
 with respect to the ensemble.  The ensemble expectation of a product of
 normal-ordered operators is its fully contracted part, so these expectations
@@ -310,6 +312,27 @@ class TinySystem:
                                 op = fs.e2(so(base + e, s), so(base + f, u), so(k, s), so(l, u))
                                 V = V + 0.5 * c * (op + op.T)
         return V
+
+    def hamiltonian(self, eri, f):
+        """1/2 sum_{pqrs} <pq|rs> {E^{pq}_{rs}} + sum_{pq} f[p][q] E^p_q over all
+        spatial orbitals (eri[p][q][r][s] = <pq|rs>; constants dropped)."""
+        fs = self.fs
+        H = sps.csr_matrix((fs.dim, fs.dim))
+        n = self.norb
+        for p in range(n):
+            for q in range(n):
+                for r in range(n):
+                    for s in range(n):
+                        c = eri[p, q, r, s]
+                        if c == 0.0:
+                            continue
+                        for a in (0, 1):
+                            for b in (0, 1):
+                                H = H + 0.5 * c * self.gno2(so(p, a), so(q, b), so(r, a), so(s, b))
+                if f[p, q] != 0.0:
+                    for a in (0, 1):
+                        H = H + f[p, q] * fs.e1(so(p, a), so(q, a))
+        return H
 
     def energy(self, V, H0, A):
         def app(psi):

@@ -657,3 +657,112 @@ def test_ladder_pair_transpose_symmetry():
     t = rng.standard_normal((nv, nv))
     C = O.ladder(Bv, np.stack([t, t.T]))
     assert np.max(np.abs(C[1] - C[0].T)) <= 1e-12 * np.max(np.abs(C))
+
+
+# ---------------------------------------------------------------------------
+# Full multi-reference PT2 energy (Eq. A4's H-bar to second order)
+# ---------------------------------------------------------------------------
+def _tiny_full_problem(nc, na, nv, sysm, use_f, seed):
+    """A problem whose integrals come from a DF factor over ALL orbitals, with
+    an off-diagonal Fock matrix (zero in the core, active and virtual diagonal
+    blocks, which make H0 = diag(eps)); returns (prob, eri, f) for the brute
+    force, which uses every block of the Hamiltonian."""
+    norb, nh = nc + na + nv, nc + na
+    rng = np.random.default_rng(seed)
+    naux = 6
+    Bf = rng.standard_normal((naux, norb, norb)) * 0.3
+    Bf = Bf + Bf.transpose(0, 2, 1)
+    eps = np.concatenate([np.sort(rng.uniform(-2, -0.3, nc)), np.sort(rng.uniform(-0.5, 0.3, na)),
+                          np.sort(rng.uniform(0.1, 2.0, nv))])
+    f = np.zeros((norb, norb))
+    if use_f:
+        f = rng.standard_normal((norb, norb)) * 0.1
+        f = f + f.T
+        for b in (slice(0, nc), slice(nc, nh), slice(nh, norb)):
+            f[b, b] = 0.0
+    prob = make_problem(nc, na, nv, naux, seed=5, nstates=1, s=0.7)
+    prob.B = np.ascontiguousarray(Bf[:, :nh, nc:])
+    prob.eps = eps
+    prob.gamma1, prob.lambda2 = sysm.gamma1, sysm.lambda2
+    prob.f_hp = f[:nh, nc:].copy() if use_f else None
+    eri = np.einsum("Qpr,Qqs->pqrs", Bf, Bf)     # <pq|rs> = (pr|qs)
+    return prob, eri, f
+
+
+@pytest.mark.parametrize("nc,na,nv,nel_act,use_f,seed", [(1, 3, 1, 2, False, 3), (1, 3, 1, 4, True, 4),
+                                                         (2, 2, 2, 2, True, 5)])
+def test_fock_space_full_pt2_energy(nc, na, nv, nel_act, use_f, seed):
+    """E^(2) = <[H, A]> + 1/2 <[[H0, A], A]> with the Hamiltonian's every block
+    (all 4-index integrals over all orbitals, the off-diagonal Fock matrix),
+    A = T - T^+ from Eqs. A6, A7 over every amplitude class, evaluated with
+    determinant-space matrices over singlet ensembles; the oracle's closed form
+    (Lambda3 from the CI vectors) must agree to rounding, and without Lambda3
+    it must differ (the 3-cumulant terms are not empty)."""
+    sysm = TinySystem(nc, na, nv, nel_act=nel_act, nstates=2, seed=seed, weights=(0.3, 0.7))
+    prob, eri, f = _tiny_full_problem(nc, na, nv, sysm, use_f, seed)
+    T2, _, _ = O.t2_general(prob)
+    T1, _, _, _ = O.t1_general(prob, T2)
+    T = sysm.cluster(T1, T2)
+    brute = sysm.energy(sysm.hamiltonian(eri, f), sysm.h0(prob.eps), T - T.T)
+    e = O.pt2_energy(prob, sysm.lambda3)
+    assert abs(e - brute) <= 1e-13 * abs(brute), (e, brute)
+    assert abs(O.pt2_energy(prob) - brute) > 1e-4 * abs(brute)
+
+
+def test_fock_space_commutator_scalar_random_operators():
+    """<[X, T]> of random normal-ordered de-excitation X and excitation T
+    (one- and two-body, pair-symmetric) against determinant space: the
+    generalised-Wick closed form holds for any operators, not only the PT2
+    amplitudes."""
+    nc, na, nv = 1, 3, 1
+    sysm = TinySystem(nc, na, nv, nel_act=2, nstates=2, seed=8, weights=(0.45, 0.55))
+    prob = make_problem(nc, na, nv, 4, seed=2, nstates=1)
+    prob.gamma1, prob.lambda2 = sysm.gamma1, sysm.lambda2
+    nh, npart = nc + na, na + nv
+    rng = np.random.default_rng(12)
+    X2 = rng.standard_normal((nh, nh, npart, npart))
+    X2 = X2 + X2.transpose(1, 0, 3, 2)
+    T2 = rng.standard_normal((nh, nh, npart, npart))
+    T2 = T2 + T2.transpose(1, 0, 3, 2)
+    T2[nc:, nc:, :na, :na] = 0.0
+    X1 = rng.standard_normal((nh, npart))
+    T1 = rng.standard_normal((nh, npart))
+    T1[nc:, :na] = 0.0
+    Xo = sysm.cluster(X1, X2).T          # E^{ij}_{ab} = (E^{ab}_{ij})^+
+    To = sysm.cluster(T1, T2)
+    brute = sysm.expect(lambda psi: Xo @ (To @ psi) - To @ (Xo @ psi))
+    e = O.commutator_scalar(prob, X1, X2, T1, T2, sysm.lambda3)
+    assert abs(e - brute) <= 1e-12 * max(1.0, abs(brute)), (e, brute)
+
+
+def test_full_pt2_energy_vv_part_is_e_vv():
+    """Restricted to the doubles whose particles are both virtual, the
+    closed form of <[X, T]> reproduces E_vv (a separate derivation through
+    the hole 2-RDM) on a CAS(6,6) problem."""
+    p = make_problem(3, 6, 12, 30, seed=6, nstates=3)
+    na = p.nact
+    T2, nu, d = O.t2_general(p)
+    keep = np.zeros_like(T2, dtype=bool)
+    keep[:, :, na:, na:] = True
+    T2v = np.where(keep, T2, 0.0)
+    X2v = np.where(keep, nu - 0.5 * d * T2, 0.0)
+    z = np.zeros((p.nh, p.np_))
+    e = 2.0 * O.commutator_scalar(p, z, X2v, z, T2v)
+    ref = O.e_vv(p)
+    assert abs(e - ref) <= 1e-12 * abs(ref)
+
+
+def test_full_pt2_energy_single_reference_is_mp2():
+    """No active orbitals, large s: E^(2) is the closed-shell MP2 energy
+    including the singles of an off-diagonal Fock matrix,
+    sum (ia|jb)[2(ia|jb) - (ib|ja)]/Delta + 2 sum |f_ia|^2/Delta_i^a."""
+    p = make_problem(5, 0, 20, 40, seed=9, nstates=1, s=1.0e3)
+    rng = np.random.default_rng(4)
+    p.f_hp = 0.05 * rng.standard_normal((p.nh, p.np_))
+    nu = np.einsum("Qia,Qjb->ijab", p.B, p.B)
+    eh, ep = O.hole_eps(p), O.particle_eps(p)
+    d = eh[:, None, None, None] + eh[None, :, None, None] - ep[None, None, :, None] - ep[None, None, None, :]
+    mp2 = np.sum(nu * (2.0 * nu - nu.transpose(0, 1, 3, 2)) / d)
+    mp2 += 2.0 * np.sum(p.f_hp ** 2 / (eh[:, None] - ep[None, :]))
+    e = O.pt2_energy(p)
+    assert abs(e - mp2) <= 1e-12 * abs(mp2), (e, mp2)
