@@ -601,6 +601,20 @@ def discarded_correction(prob, no, nkept, e_mo=None):
     return e_mo - e_fno, e_fno, eps_new
 
 
+def discarded_correction_mr(prob, no, nkept, lambda3=None, e_mo=None):
+    """Eq. 11 with the full second-order energy: E^(2)(MO) - E^(2)(FNO), the
+    FNO problem being the kept NOs recanonicalised (B, the virtual orbital
+    energies and the virtual columns of f_hp rotated; the active particles
+    stay).  This carries the active-labelled parts of the correction (the
+    doubles with an active particle, the singles) beside the vv part.
+    Returns (dE, E_fno, eps')."""
+    if e_mo is None:
+        e_mo = pt2_energy(prob, lambda3)
+    U, eps_new = recanonicalize(prob, no, nkept)
+    e_fno = pt2_energy(fno_problem(prob, U, eps_new), lambda3)
+    return e_mo - e_fno, e_fno, eps_new
+
+
 # --------------------------------------------------------------------------
 # Particle-particle ladder of Eq. 6 in the truncated virtual basis
 # --------------------------------------------------------------------------

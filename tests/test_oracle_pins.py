@@ -766,3 +766,35 @@ def test_full_pt2_energy_single_reference_is_mp2():
     mp2 += 2.0 * np.sum(p.f_hp ** 2 / (eh[:, None] - ep[None, :]))
     e = O.pt2_energy(p)
     assert abs(e - mp2) <= 1e-12 * abs(mp2), (e, mp2)
+
+
+def test_full_correction_limits():
+    """Eq. 11 with the full energy: keeping every NO gives 0; keeping none
+    leaves the problem with active particles only, whose energy is that of
+    the same problem sliced to no virtuals (a separate construction)."""
+    p = make_problem(3, 4, 14, 30, seed=12, nstates=2)
+    rng = np.random.default_rng(2)
+    p.f_hp = 0.05 * rng.standard_normal((p.nh, p.np_))
+    ons, no = O.natural_orbitals(O.dvv(p))
+    de, _, _ = O.discarded_correction_mr(p, no, p.nvir)
+    assert abs(de) <= 1e-12 * abs(O.pt2_energy(p))
+    from copy import copy
+    q = copy(p)
+    q.nvir = 0
+    q.B = np.ascontiguousarray(p.B[:, :, : p.nact])
+    q.eps = p.eps[: p.ncore + p.nact]
+    q.f_hp = p.f_hp[:, : p.nact]
+    de0, efno, _ = O.discarded_correction_mr(p, no, 0)
+    assert abs(efno - O.pt2_energy(q)) <= 1e-13 * max(1.0, abs(efno))
+    assert abs(de0 - (O.pt2_energy(p) - O.pt2_energy(q))) <= 1e-12 * abs(de0)
+    # a kept subset of the semicanonical virtuals (NOs = identity columns)
+    # equals the problem sliced to those virtuals
+    eye = np.eye(p.nvir)
+    k = 9
+    _, efk, _ = O.discarded_correction_mr(p, eye, k)
+    r = copy(p)
+    r.nvir = k
+    r.B = np.ascontiguousarray(p.B[:, :, : p.nact + k])
+    r.eps = p.eps[: p.ncore + p.nact + k]
+    r.f_hp = p.f_hp[:, : p.nact + k]
+    assert abs(efk - O.pt2_energy(r)) <= 1e-12 * abs(efk)
