@@ -648,6 +648,7 @@ def main():
                    "cut_margins": [cut_margins(ons_last, c, res[c][0]) for c in cuts]},
     }
     if not args.no_sub:
+        line["mr_energy"] = mr_energy_timing(pkg, p, gp, dev)
         line["sub_results"] = sub_results(pkg, dev, args.nslices)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, [res[c][0] for c in cuts])
@@ -655,6 +656,36 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def mr_energy_timing(pkg, p, gp, dev, steps=2):
+    """The full second-order energy over every amplitude class
+    (dsrg_fno_pt2_energy_mr) on the headline workload, with a seeded synthetic
+    3-cumulant: E_vv on the digit-plane path, the rest (doubles with an active
+    particle, singles, cumulant couplings) in float64; timed beside E_vv alone.
+    rest_gemm_flops: the float64 integral GEMM of the rest, 2 nh np nh nact naux."""
+    import torch
+    from synth.problems import random_cumulant3
+    l3 = torch.from_numpy(random_cumulant3(p.nact, 2)).to(dev) if p.nact else None
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps / 1e3, r
+
+    s_full, (e2, evv) = timed(lambda: pkg.dsrg_fno_pt2_energy_mr(gp, l3))
+    s_vv, _ = timed(lambda: pkg.dsrg_fno_pt2_energy(gp))
+    flops = 2.0 * p.nh * p.np_ * p.nh * p.nact * p.naux
+    return {"s_full": s_full, "s_vv_only": s_vv, "s_rest": s_full - s_vv, "e2": e2, "e_vv": evv,
+            "e_rest": e2 - evv, "lambda3": "seeded synthetic 3-cumulant (scale 0.03)", "steps": steps,
+            "rest_gemm_flops": flops}
 
 
 SUB_SINGLE = "sa_cas12_ncore95_nvir1000_naux4200"

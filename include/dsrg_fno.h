@@ -8,7 +8,9 @@
  * vv-class second-order energy (scalar of Eq. A4), diagonalises that block
  * into natural orbitals (Eq. 8), truncates the virtual NOs (Eqs. 9, 10 and
  * the near-degeneracy rule of Sec. 2), and forms the second-order correction
- * for the discarded virtuals (scalar part of Eq. 11).
+ * for the discarded virtuals (scalar part of Eq. 11).  The full second-order
+ * energy over every amplitude class, and its correction, are available too
+ * (dsrg_fno_pt2_energy_mr, dsrg_fno_discarded_correction_mr).
  *
  * Conventions shared by every entry point
  *   - nh = ncore + nact holes (core first), np = nact + nvir particles
@@ -102,6 +104,29 @@ typedef struct {
  * virtual; Eq. A4 scalar restricted to them; in the single-reference limit
  * the whole DSRG-PT2 energy).  e2_out: host scalar. */
 int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stream);
+
+/* Full second-order SA-DSRG energy E^(2) = <[H, A]>_0 + 1/2 <[[H0, A], A]>_0,
+ * the correlation part of <H-bar^[2]> (the second-order Hamiltonian stated
+ * with Eq. A4), over every first-order amplitude class of Eqs. A6, A7: the
+ * doubles with active or virtual particles and core or active holes (the
+ * all-active block excluded) and the singles, with the off-diagonal Fock
+ * f^i_a of f_hp (NULL: zero).  The scalar is evaluated by the generalised
+ * Wick theorem in the Mukherjee-Kutzelnigg normal order of the ensemble:
+ * Gamma1 and Lambda2 always, the 3-cumulant when `lambda3` is given.
+ *   lambda3  device [nact]^6 (layout as in dsrg_fno_vv_opdm_lambda3), or NULL:
+ *            the terms with one 3-cumulant are then dropped, which Sec. 2
+ *            allows when the 1-RDM drops them too (dsrg_fno_vv_opdm); read only.
+ *   e2_out   host: E^(2).
+ *   evv_out  host, may be NULL: its vv-class part E_vv (dsrg_fno_pt2_energy).
+ * E_vv runs on the path that prob->precision selects; the rest (the doubles
+ * with an active particle, the singles, their cumulant couplings) in float64.
+ * In the single-reference limit (nact = 0) E^(2) = E_vv plus the singles of
+ * f_hp.  Errors as for dsrg_fno_pt2_energy; a host lambda3 gives
+ * DSRG_FNO_ERR_ARG, a non-finite one DSRG_FNO_ERR_NONFINITE.  Device
+ * workspace: about 32 nh^2 np nact bytes beyond the E_vv pass (grow-only,
+ * freed by dsrg_fno_release).  Synchronises `stream`. */
+int dsrg_fno_pt2_energy_mr(const dsrg_fno_problem* prob, const double* lambda3, double* e2_out,
+                           double* evv_out, void* stream);
 
 /* D_vv = virtual-virtual block of the unrelaxed PT2 1-RDM correction, Eq. A12
  * terms 1-12 (the Lambda3 term 13 is not formed, as Sec. 2 allows when the
@@ -258,6 +283,27 @@ int dsrg_fno_naf(int32_t nh, int32_t np, int32_t naux, const double* B_hp, doubl
 int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept,
                                   const double* no, const double* e2_mo_in, double* de_out,
                                   double* e2_fno_out, double* eps_fno_out, void* stream);
+
+/* Eq. 11 with the full second-order energy of dsrg_fno_pt2_energy_mr:
+ * E^(2)(MO) - E^(2)(FNO), where the FNO problem keeps the active particles
+ * and the recanonicalised kept NOs (B, the virtual orbital energies and the
+ * virtual columns of f_hp rotated to them).  Beside the vv part this carries
+ * the active-labelled parts of the correction (the doubles with an active
+ * particle, the singles and their cumulant couplings; Sec. 2 costs them as
+ * O(N_V^2 (N_C^2 + N_A^4))).
+ *   lambda3     device [nact]^6 or NULL, as in dsrg_fno_pt2_energy_mr (used in
+ *               both bases).
+ *   e2_mo_in    host or NULL: the full E^(2)(MO) of the same problem (as
+ *               returned by dsrg_fno_pt2_energy_mr with the same lambda3);
+ *               NULL makes the call evaluate it.
+ *   de_out      host: E^(2)(MO) - E^(2)(FNO).
+ *   e2_fno_out  host or NULL: E^(2)(FNO); with nkept = 0 it is the energy of
+ *               the active particles alone (not zero).
+ *   Other arguments and errors as for dsrg_fno_discarded_correction; the vv
+ *   parts follow prob->precision, the rest is float64. */
+int dsrg_fno_discarded_correction_mr(const dsrg_fno_problem* prob, const double* lambda3, int32_t nkept,
+                                     const double* no, const double* e2_mo_in, double* de_out,
+                                     double* e2_fno_out, double* eps_fno_out, void* stream);
 
 /* State-averaged densities of Eq. A1 from per-state spin-free densities,
  * host arrays (a helper for preparing dsrg_fno_problem inputs):

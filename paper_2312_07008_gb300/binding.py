@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(HERE, "libdsrg_fno.so")
 
 EXPORTED = (
     "dsrg_fno_pt2_energy",
+    "dsrg_fno_pt2_energy_mr",
+    "dsrg_fno_discarded_correction_mr",
     "dsrg_fno_vv_opdm",
     "dsrg_fno_vv_opdm_lambda3",
     "dsrg_fno_sa_lambda3",
@@ -99,6 +101,9 @@ def load(path: str = LIB_PATH):
     vp, d, i32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32
     P = ctypes.POINTER(CProblem)
     lib.dsrg_fno_pt2_energy.argtypes = [P, ctypes.POINTER(d), vp]
+    lib.dsrg_fno_pt2_energy_mr.argtypes = [P, vp, ctypes.POINTER(d), ctypes.POINTER(d), vp]
+    lib.dsrg_fno_discarded_correction_mr.argtypes = [P, vp, i32, vp, ctypes.POINTER(d), ctypes.POINTER(d),
+                                                     ctypes.POINTER(d), vp, vp]
     lib.dsrg_fno_vv_opdm.argtypes = [P, vp, ctypes.POINTER(d), vp]
     lib.dsrg_fno_vv_opdm_lambda3.argtypes = [P, vp, vp, ctypes.POINTER(d), vp]
     lib.dsrg_fno_sa_lambda3.argtypes = [i32, i32, ctypes.POINTER(d), vp, vp, vp, vp, vp]
@@ -208,6 +213,17 @@ def dsrg_fno_pt2_energy(prob: Problem, stream=None) -> float:
     return e.value
 
 
+def dsrg_fno_pt2_energy_mr(prob: Problem, lambda3=None, stream=None):
+    """Full E^(2) over every amplitude class; lambda3 (device [nact]^6) or None.
+    Returns (E^(2), its vv-class part E_vv)."""
+    e = ctypes.c_double()
+    ev = ctypes.c_double()
+    _check("dsrg_fno_pt2_energy_mr",
+           load().dsrg_fno_pt2_energy_mr(ctypes.byref(prob.c), _ptr(lambda3) if lambda3 is not None else None,
+                                         ctypes.byref(e), ctypes.byref(ev), _stream(stream)))
+    return e.value, ev.value
+
+
 def dsrg_fno_vv_opdm(prob: Problem, dvv_out, stream=None) -> float:
     e = ctypes.c_double()
     _check("dsrg_fno_vv_opdm", load().dsrg_fno_vv_opdm(ctypes.byref(prob.c), _ptr(dvv_out), ctypes.byref(e),
@@ -283,6 +299,18 @@ def dsrg_fno_discarded_correction(prob: Problem, nkept, no, e2_mo=None, eps_fno_
     _check("dsrg_fno_discarded_correction",
            load().dsrg_fno_discarded_correction(ctypes.byref(prob.c), int(nkept), _ptr(no), emo, ctypes.byref(de),
                                                 ctypes.byref(ef), _ptr(eps_fno_out), _stream(stream)))
+    return de.value, ef.value
+
+
+def dsrg_fno_discarded_correction_mr(prob: Problem, nkept, no, lambda3=None, e2_mo=None, eps_fno_out=None,
+                                     stream=None):
+    """Eq. 11 with the full E^(2): returns (E^(2)(MO) - E^(2)(FNO), E^(2)(FNO))."""
+    de, ef = ctypes.c_double(), ctypes.c_double()
+    emo = None if e2_mo is None else ctypes.byref(ctypes.c_double(e2_mo))
+    _check("dsrg_fno_discarded_correction_mr",
+           load().dsrg_fno_discarded_correction_mr(ctypes.byref(prob.c), _ptr(lambda3) if lambda3 is not None else None,
+                                                   int(nkept), _ptr(no), emo, ctypes.byref(de), ctypes.byref(ef),
+                                                   _ptr(eps_fno_out), _stream(stream)))
     return de.value, ef.value
 
 

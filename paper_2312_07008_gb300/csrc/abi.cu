@@ -577,6 +577,42 @@ int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
                      st);
 }
 
+int impl_pt2_energy_mr(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, const double* l3, double* e2_out,
+                       double* evv_out, cudaStream_t st) {
+  int s = validate(prob);
+  if (s) return s;
+  if (!e2_out) return DSRG_FNO_ERR_ARG;
+  if (prob->nact == 0) l3 = nullptr;
+  if (l3 && !is_device_ptr(l3)) return DSRG_FNO_ERR_ARG;
+  const Geometry g = geometry_of(prob);
+  const int ks = slices_of(prob);
+  const int2 pform = pair_form_of(prob, ks);
+  const size_t mr = mr_energy_work_doubles(g);
+  DSRG_TRY(ws_reserve(ws, ws_bytes(8, sizeof(int)) + std::max(energy_pass_bytes(g, ks, pform, budget), doubles(mr))));
+  int* flag = ws_take<int>(ws, 8);
+  DSRG_TRY(check_inputs_finite(prob, flag, st));
+  if (l3) {
+    const long n3 = (long)g.na * g.na * g.na;
+    int h = 0;
+    DSRG_TRY(check_finite(l3, n3 * n3, flag, st));
+    DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSRG_CUDA(cudaStreamSynchronize(st));
+    if (h) return DSRG_FNO_ERR_NONFINITE;
+  }
+  const size_t base = ws.off;
+  double evv = 0.0;
+  DSRG_TRY(energy_pass(g, ks, pform, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, base, budget, &evv, st));
+  ws.off = base;
+  double* work = ws_take<double>(ws, mr);
+  if (!work) return DSRG_FNO_ERR_NOMEM;
+  double rest = 0.0;
+  DSRG_TRY(mr_energy_rest(g, prob->B_hp, prob->eps, prob->f_hp, prob->gamma1, prob->lambda2, l3, work, &rest, st));
+  if (!isfinite(evv) || !isfinite(rest)) return DSRG_FNO_ERR_NONFINITE;
+  *e2_out = evv + rest;
+  if (evv_out) *evv_out = evv;
+  return DSRG_FNO_OK;
+}
+
 int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
                  cudaStream_t st, const double* l3) {
   int s = validate(prob);
@@ -673,7 +709,7 @@ int impl_truncate(Workspace& ws, int32_t nvir, const double* dvv, int32_t mode, 
 
 int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, int32_t nkept,
                            const double* no, const double* e2_mo_in, double* de_out, double* e2_fno_out,
-                           double* eps_fno_out, cudaStream_t st) {
+                           double* eps_fno_out, cudaStream_t st, const CorrectionMR* mr) {
   int s = validate(prob);
   if (s) return s;
   if (!de_out || !no || nkept < 0 || nkept > prob->nvir || !is_device_ptr(no)) return DSRG_FNO_ERR_ARG;
@@ -701,9 +737,20 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
   if (kx && nk > 0)
     xform = ws_bytes((size_t)kx * rows * kpv, 2) + ws_bytes(rows, sizeof(int)) + ws_bytes((size_t)kx * nk * kpv, 2) +
             ws_bytes(nk, sizeof(int)) + ws_bytes(8, sizeof(int));
-  DSRG_TRY(ws_reserve(ws, fixed + std::max(std::max(pass_mo, pass_f), xform)));
+  // full-energy form: the rest terms of both bases (their work overlaps the passes) and f_hp rotated
+  const size_t mr_work = mr ? doubles(mr_energy_work_doubles(g)) : 0;
+  const size_t ff_bytes = mr ? doubles((size_t)g.nh * gf.np + 1) : 0;
+  DSRG_TRY(ws_reserve(ws, fixed + ff_bytes + std::max(std::max(pass_mo, pass_f), std::max(xform, mr_work))));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
+  if (mr && mr->l3) {
+    const long n3 = (long)g.na * g.na * g.na;
+    int h = 0;
+    DSRG_TRY(check_finite(mr->l3, n3 * n3, flag, st));
+    DSRG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSRG_CUDA(cudaStreamSynchronize(st));
+    if (h) return DSRG_FNO_ERR_NONFINITE;
+  }
   double* Wt = ws_take<double>(ws, (size_t)nv * nk);
   double* U = ws_take<double>(ws, (size_t)nv * nk);
   double* F = ws_take<double>(ws, nk2);
@@ -714,12 +761,23 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
   double* Bf = ws_take<double>(ws, (size_t)rows * gf.np + 1);
   double* epsf = ws_take<double>(ws, g.nh + nk + 1);
   double* evals = ws_take<double>(ws, nk + 1);
+  double* ff = mr ? ws_take<double>(ws, (size_t)g.nh * gf.np + 1) : nullptr;
   const size_t base = ws.off;
   double e_mo = 0.0;
   if (e2_mo_in) e_mo = *e2_mo_in;
-  else
+  else {
     DSRG_TRY(energy_pass(g, ks, pform, prob->B_hp, prob->eps, prob->gamma1, prob->lambda2, ws, base, budget, &e_mo,
                          st));
+    if (mr) {
+      ws.off = base;
+      double* work = ws_take<double>(ws, mr_energy_work_doubles(g));
+      double rest = 0.0;
+      if (!work) return DSRG_FNO_ERR_NOMEM;
+      DSRG_TRY(mr_energy_rest(g, prob->B_hp, prob->eps, prob->f_hp, prob->gamma1, prob->lambda2, mr->l3, work, &rest,
+                              st));
+      e_mo += rest;
+    }
+  }
   double e_f = 0.0;
   if (nk > 0) {
     // F' = Vk^T diag(eps_v) Vk, recanonicalised: F' W = W eps'
@@ -758,6 +816,29 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
     if (eps_fno_out)
       DSRG_CUDA(cudaMemcpyAsync(eps_fno_out, evals, sizeof(double) * nk, cudaMemcpyDeviceToDevice, st));
     DSRG_TRY(energy_pass(gf, ks, pform, Bf, epsf, prob->gamma1, prob->lambda2, ws, base, budget, &e_f, st));
+  }
+  if (mr) {
+    // E^(2)(FNO) beyond its vv part: the active particles stay, the kept
+    // virtuals are the recanonicalised NOs (with nkept = 0 only the active
+    // particles are left); f_hp's virtual columns rotate with them.
+    if (nk == 0) {
+      DSRG_TRY(copy_active(rows, g.na, g.np, gf.np, prob->B_hp, Bf, st));
+      DSRG_CUDA(cudaMemcpyAsync(epsf, prob->eps, sizeof(double) * g.nh, cudaMemcpyDeviceToDevice, st));
+    }
+    const double* f_fno = nullptr;
+    if (prob->f_hp) {
+      DSRG_TRY(copy_active(g.nh, g.na, g.np, gf.np, prob->f_hp, ff, st));
+      if (nk > 0)
+        DSRG_TRY(gemm_f64(g.nh, nk, nv, 1.0, prob->f_hp + g.na, g.np, true, U, nk, false, 0.0, ff + g.na, gf.np, 1,
+                          0, 0, 0, st));
+      f_fno = ff;
+    }
+    ws.off = base;
+    double* work = ws_take<double>(ws, mr_energy_work_doubles(gf));
+    double rest = 0.0;
+    if (!work) return DSRG_FNO_ERR_NOMEM;
+    DSRG_TRY(mr_energy_rest(gf, Bf, epsf, f_fno, prob->gamma1, prob->lambda2, mr->l3, work, &rest, st));
+    e_f += rest;
   }
   if (!isfinite(e_mo) || !isfinite(e_f)) return DSRG_FNO_ERR_NONFINITE;
   *de_out = e_mo - e_f;
@@ -809,6 +890,13 @@ int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stre
   return impl_pt2_energy(ws, plan_budget(ws), prob, e2_out, (cudaStream_t)stream);
 }
 
+int dsrg_fno_pt2_energy_mr(const dsrg_fno_problem* prob, const double* lambda3, double* e2_out, double* evv_out,
+                           void* stream) {
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  return impl_pt2_energy_mr(ws, plan_budget(ws), prob, lambda3, e2_out, evv_out, (cudaStream_t)stream);
+}
+
 int dsrg_fno_vv_opdm(const dsrg_fno_problem* prob, double* dvv_out, double* e2_out, void* stream) {
   std::lock_guard<std::mutex> lk(workspace_mutex());
   Workspace& ws = workspace_for_current_device();
@@ -854,6 +942,17 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept, c
   Workspace& ws = workspace_for_current_device();
   return impl_correction(ws, plan_budget(ws), prob, nkept, no, e2_mo_in, de_out, e2_fno_out, eps_fno_out,
                          (cudaStream_t)stream);
+}
+
+int dsrg_fno_discarded_correction_mr(const dsrg_fno_problem* prob, const double* lambda3, int32_t nkept,
+                                     const double* no, const double* e2_mo_in, double* de_out, double* e2_fno_out,
+                                     double* eps_fno_out, void* stream) {
+  if (lambda3 && prob && prob->nact > 0 && !is_device_ptr(lambda3)) return DSRG_FNO_ERR_ARG;
+  CorrectionMR mr{prob && prob->nact > 0 ? lambda3 : nullptr};
+  std::lock_guard<std::mutex> lk(workspace_mutex());
+  Workspace& ws = workspace_for_current_device();
+  return impl_correction(ws, plan_budget(ws), prob, nkept, no, e2_mo_in, de_out, e2_fno_out, eps_fno_out,
+                         (cudaStream_t)stream, &mr);
 }
 
 }  // extern "C"

@@ -93,7 +93,7 @@ inline size_t ws_bytes(size_t count, size_t elt) { return ((count * elt) + 255) 
 // For x = c s Delta^2 below 1e-3 the Taylor series of 1 - exp(-x) is used
 // (truncation error below x^5/720 relative); Delta = 0 gives 0.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ double regularizer(double delta, double cs) {
+__host__ __device__ __forceinline__ double regularizer(double delta, double cs) {
   const double x = cs * delta * delta;
   if (x < 1.0e-3) {
     const double p = 1.0 - x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0))));

@@ -183,19 +183,31 @@ int check_finite(const double* x, long n, int* flag, cudaStream_t st);
 // Whether p is device (or managed) memory; cudaPointerGetAttributes allocates nothing.
 bool is_device_ptr(const void* p);
 
+// Full multi-reference PT2 energy beyond E_vv, float64 (energy_mr.cu).
+size_t mr_energy_work_doubles(const Geometry& g);
+int mr_energy_rest(const Geometry& g, const double* B, const double* eps, const double* f_hp, const double* g1,
+                   const double* l2, const double* l3, double* work, double* e_out, cudaStream_t st);
+
 // Single-instance pipeline stages on an explicit workspace (abi.cu); the C
 // entry points call them on the per-device workspace, the batch runner on
 // its workers' workspaces.  `budget`: device bytes a pass may plan for.
 size_t device_budget(size_t held);
 void release_batch_pools();  // batch.cu
 int impl_pt2_energy(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* e2_out, cudaStream_t st);
+// E^(2) over every class: E_vv on the selected path plus mr_energy_rest; l3 may be null
+int impl_pt2_energy_mr(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, const double* l3, double* e2_out,
+                       double* evv_out, cudaStream_t st);
 // l3: device [nact]^6 3-cumulant for Eq. A12 term 13, or null (terms 1-12 only)
 int impl_vv_opdm(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, double* dvv_out, double* e2_out,
                  cudaStream_t st, const double* l3 = nullptr);
 int impl_truncate(Workspace& ws, int32_t nvir, const double* dvv, int32_t mode, double threshold, double degen_ratio,
                   double* on_out, double* no_out, int32_t* nkept_out, cudaStream_t st);
+// Full-energy form of the correction (dsrg_fno_discarded_correction_mr): l3 may be null.
+struct CorrectionMR {
+  const double* l3;
+};
 int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, int32_t nkept, const double* no,
                     const double* e2_mo_in, double* de_out, double* e2_fno_out, double* eps_fno_out,
-                    cudaStream_t st);
+                    cudaStream_t st, const CorrectionMR* mr = nullptr);
 
 }  // namespace dsrg
