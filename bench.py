@@ -682,10 +682,19 @@ def mr_energy_timing(pkg, p, gp, dev, steps=2):
 
     s_full, (e2, evv) = timed(lambda: pkg.dsrg_fno_pt2_energy_mr(gp, l3))
     s_vv, _ = timed(lambda: pkg.dsrg_fno_pt2_energy(gp))
+    # phases of one more call: the integral GEMM (digit planes) and the element stages of the rest
+    pkg.dsrg_fno_profile_enable(True)
+    pkg.dsrg_fno_pt2_energy_mr(gp, l3)
+    torch.cuda.synchronize()
+    pkg.dsrg_fno_profile_enable(False)
+    ph = {nm: pkg.dsrg_fno_profile_query(nm)[0] / 1e3 for nm in ("phase_mr_integrals", "phase_mr_terms")}
+    g_ms, _, g_fl = pkg.dsrg_fno_profile_query("sliced_gemm_plain")
     flops = 2.0 * p.nh * p.np_ * p.nh * p.nact * p.naux
     return {"s_full": s_full, "s_vv_only": s_vv, "s_rest": s_full - s_vv, "e2": e2, "e_vv": evv,
             "e_rest": e2 - evv, "lambda3": "seeded synthetic 3-cumulant (scale 0.03)", "steps": steps,
-            "rest_gemm_flops": flops}
+            "s_rest_integrals": ph["phase_mr_integrals"], "s_rest_terms": ph["phase_mr_terms"],
+            "rest_gemm_flops": flops, "rest_gemm_ms": g_ms,
+            "rest_gemm_tflops_executed": (g_fl / (g_ms / 1e3) / 1e12) if g_ms > 0 else None}
 
 
 SUB_SINGLE = "sa_cas12_ncore95_nvir1000_naux4200"

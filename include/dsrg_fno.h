@@ -119,11 +119,15 @@ int dsrg_fno_pt2_energy(const dsrg_fno_problem* prob, double* e2_out, void* stre
  *   e2_out   host: E^(2).
  *   evv_out  host, may be NULL: its vv-class part E_vv (dsrg_fno_pt2_energy).
  * E_vv runs on the path that prob->precision selects; the rest (the doubles
- * with an active particle, the singles, their cumulant couplings) in float64.
+ * with an active particle, the singles, their cumulant couplings) in float64,
+ * except that outside the FP64 form its integrals <ay|ij> (one contraction
+ * over the auxiliary index, rows (i, a) against (j, y), y active) run on the
+ * digit-plane tensor-core path when naux >= 256.
  * In the single-reference limit (nact = 0) E^(2) = E_vv plus the singles of
  * f_hp.  Errors as for dsrg_fno_pt2_energy; a host lambda3 gives
  * DSRG_FNO_ERR_ARG, a non-finite one DSRG_FNO_ERR_NONFINITE.  Device
- * workspace: about 32 nh^2 np nact bytes beyond the E_vv pass (grow-only,
+ * workspace: about 32 nh^2 np nact bytes beyond the E_vv pass, plus the digit
+ * planes of B (2 nslices nh np naux bytes) on the tensor-core path (grow-only,
  * freed by dsrg_fno_release).  Synchronises `stream`. */
 int dsrg_fno_pt2_energy_mr(const dsrg_fno_problem* prob, const double* lambda3, double* e2_out,
                            double* evv_out, void* stream);
@@ -299,8 +303,8 @@ int dsrg_fno_discarded_correction(const dsrg_fno_problem* prob, int32_t nkept,
  *   de_out      host: E^(2)(MO) - E^(2)(FNO).
  *   e2_fno_out  host or NULL: E^(2)(FNO); with nkept = 0 it is the energy of
  *               the active particles alone (not zero).
- *   Other arguments and errors as for dsrg_fno_discarded_correction; the vv
- *   parts follow prob->precision, the rest is float64. */
+ *   Other arguments and errors as for dsrg_fno_discarded_correction; both
+ *   energies are evaluated as in dsrg_fno_pt2_energy_mr. */
 int dsrg_fno_discarded_correction_mr(const dsrg_fno_problem* prob, const double* lambda3, int32_t nkept,
                                      const double* no, const double* e2_mo_in, double* de_out,
                                      double* e2_fno_out, double* eps_fno_out, void* stream);

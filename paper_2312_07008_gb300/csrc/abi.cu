@@ -587,7 +587,7 @@ int impl_pt2_energy_mr(Workspace& ws, size_t budget, const dsrg_fno_problem* pro
   const Geometry g = geometry_of(prob);
   const int ks = slices_of(prob);
   const int2 pform = pair_form_of(prob, ks);
-  const size_t mr = mr_energy_work_doubles(g);
+  const size_t mr = mr_energy_work_doubles(g, ks);
   DSRG_TRY(ws_reserve(ws, ws_bytes(8, sizeof(int)) + std::max(energy_pass_bytes(g, ks, pform, budget), doubles(mr))));
   int* flag = ws_take<int>(ws, 8);
   DSRG_TRY(check_inputs_finite(prob, flag, st));
@@ -606,7 +606,7 @@ int impl_pt2_energy_mr(Workspace& ws, size_t budget, const dsrg_fno_problem* pro
   double* work = ws_take<double>(ws, mr);
   if (!work) return DSRG_FNO_ERR_NOMEM;
   double rest = 0.0;
-  DSRG_TRY(mr_energy_rest(g, prob->B_hp, prob->eps, prob->f_hp, prob->gamma1, prob->lambda2, l3, work, &rest, st));
+  DSRG_TRY(mr_energy_rest(g, ks, prob->B_hp, prob->eps, prob->f_hp, prob->gamma1, prob->lambda2, l3, work, &rest, st));
   if (!isfinite(evv) || !isfinite(rest)) return DSRG_FNO_ERR_NONFINITE;
   *e2_out = evv + rest;
   if (evv_out) *evv_out = evv;
@@ -738,7 +738,7 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
     xform = ws_bytes((size_t)kx * rows * kpv, 2) + ws_bytes(rows, sizeof(int)) + ws_bytes((size_t)kx * nk * kpv, 2) +
             ws_bytes(nk, sizeof(int)) + ws_bytes(8, sizeof(int));
   // full-energy form: the rest terms of both bases (their work overlaps the passes) and f_hp rotated
-  const size_t mr_work = mr ? doubles(mr_energy_work_doubles(g)) : 0;
+  const size_t mr_work = mr ? doubles(mr_energy_work_doubles(g, ks)) : 0;
   const size_t ff_bytes = mr ? doubles((size_t)g.nh * gf.np + 1) : 0;
   DSRG_TRY(ws_reserve(ws, fixed + ff_bytes + std::max(std::max(pass_mo, pass_f), std::max(xform, mr_work))));
   int* flag = ws_take<int>(ws, 8);
@@ -770,10 +770,10 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
                          st));
     if (mr) {
       ws.off = base;
-      double* work = ws_take<double>(ws, mr_energy_work_doubles(g));
+      double* work = ws_take<double>(ws, mr_energy_work_doubles(g, ks));
       double rest = 0.0;
       if (!work) return DSRG_FNO_ERR_NOMEM;
-      DSRG_TRY(mr_energy_rest(g, prob->B_hp, prob->eps, prob->f_hp, prob->gamma1, prob->lambda2, mr->l3, work, &rest,
+      DSRG_TRY(mr_energy_rest(g, ks, prob->B_hp, prob->eps, prob->f_hp, prob->gamma1, prob->lambda2, mr->l3, work, &rest,
                               st));
       e_mo += rest;
     }
@@ -834,10 +834,10 @@ int impl_correction(Workspace& ws, size_t budget, const dsrg_fno_problem* prob, 
       f_fno = ff;
     }
     ws.off = base;
-    double* work = ws_take<double>(ws, mr_energy_work_doubles(gf));
+    double* work = ws_take<double>(ws, mr_energy_work_doubles(gf, ks));
     double rest = 0.0;
     if (!work) return DSRG_FNO_ERR_NOMEM;
-    DSRG_TRY(mr_energy_rest(gf, Bf, epsf, f_fno, prob->gamma1, prob->lambda2, mr->l3, work, &rest, st));
+    DSRG_TRY(mr_energy_rest(gf, ks, Bf, epsf, f_fno, prob->gamma1, prob->lambda2, mr->l3, work, &rest, st));
     e_f += rest;
   }
   if (!isfinite(e_mo) || !isfinite(e_f)) return DSRG_FNO_ERR_NONFINITE;

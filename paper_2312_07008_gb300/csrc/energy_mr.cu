@@ -1,10 +1,13 @@
 // Full multi-reference PT2 energy: the part beyond E_vv (every doubles class
-// with an active particle, the singles, and their cumulant couplings), float64.
+// with an active particle, the singles, and their cumulant couplings); the
+// element stages and sums in float64.
 //
 // Order of the stages (element bodies and the tensor layouts in mr_terms.cuh):
 //   1. BA[Q][j][y] = B[Q][j][y] for the active particles y (gather), and the
-//      integrals <ay|ij> = sum_Q B[Q][i][a] BA[Q][j][y] as one float64 GEMM
-//      (M = nh np rows (i, a), N = nh na columns (j, y), K = naux).
+//      integrals <ay|ij> = sum_Q B[Q][i][a] BA[Q][j][y] as one GEMM (M = nh np
+//      rows (i, a), N = nh na columns (j, y), K = naux): in the fast form on
+//      the tensor cores from exact bf16 digit planes of both operands (the
+//      plain mode of the digit-plane contraction kernel), else float64.
 //   2. Eq. A7 amplitudes tp and the vertex xp; Eq. A6 singles t1 and x1.
 //   3. The images of T under Theta (particles) and Gamma (holes): z1, tpp,
 //      z2, z3, g2t, w3, tt1, gt1.
@@ -90,15 +93,27 @@ MRSizes mr_sizes(const Geometry& g) {
 
 }  // namespace
 
-size_t mr_energy_work_doubles(const Geometry& g) {
+// doubles of a buffer, rounded up to 256 bytes so that every carved buffer stays 256-byte aligned
+static size_t mr_dbl(size_t bytes) { return (bytes + 255) / 256 * 32; }
+
+static bool mr_tensor_gemm(const Geometry& g, int ks) { return ks > 0 && g.na > 0 && g.nq >= SLICED_MIN_K; }
+
+size_t mr_energy_work_doubles(const Geometry& g, int ks) {
   const MRSizes z = mr_sizes(g);
   // nu (reused for tpp), tp, xp, z1; z2, z3; g2t, w3; t1, x1, tt1; gt1; BA; 2 x partials
-  return 4 * (size_t)z.n4 + 2 * (size_t)z.n4a + z.ng2t + z.nw3 + 3 * (size_t)z.n1 + z.ngt1 + z.nba +
-         2 * (size_t)MR_EBLOCKS + 16;
+  size_t n = 4 * mr_dbl(8 * (size_t)z.n4) + 2 * mr_dbl(8 * (size_t)z.n4a) + mr_dbl(8 * (size_t)z.ng2t) +
+             mr_dbl(8 * (size_t)z.nw3) + 3 * mr_dbl(8 * (size_t)z.n1) + mr_dbl(8 * (size_t)z.ngt1) +
+             mr_dbl(8 * (size_t)z.nba) + mr_dbl(8 * (2 * (size_t)MR_EBLOCKS + 16));
+  if (mr_tensor_gemm(g, ks)) {
+    const size_t kp = pad64(g.nq), ra = (size_t)g.nh * g.np, rb = (size_t)g.nh * g.na;
+    n += mr_dbl(2 * (size_t)ks * ra * kp) + mr_dbl(2 * (size_t)ks * rb * kp) + mr_dbl(4 * (ra + rb)) + mr_dbl(32);
+  }
+  return n;
 }
 
-int mr_energy_rest(const Geometry& g, const double* B, const double* eps, const double* f_hp, const double* g1,
-                   const double* l2, const double* l3, double* work, double* e_out, cudaStream_t st) {
+int mr_energy_rest(const Geometry& g, int ks, const double* B, const double* eps, const double* f_hp,
+                   const double* g1, const double* l2, const double* l3, double* work, double* e_out,
+                   cudaStream_t st) {
   *e_out = 0.0;
   if (g.na == 0 && !f_hp) return DSRG_FNO_OK;
   const MRSizes z = mr_sizes(g);
@@ -115,35 +130,26 @@ int mr_energy_rest(const Geometry& g, const double* B, const double* eps, const 
   A.l2 = g.na ? l2 : nullptr;
   A.l3 = g.na ? l3 : nullptr;
   double* p = work;
-  double* nu = p;
-  p += z.n4;
-  A.tp = p;
-  p += z.n4;
-  A.xp = p;
-  p += z.n4;
-  A.z1 = p;
-  p += z.n4;
-  A.z2 = p;
-  p += z.n4a;
-  A.z3 = p;
-  p += z.n4a;
-  A.g2t = p;
-  p += z.ng2t;
-  A.w3 = p;
-  p += z.nw3;
-  A.t1 = p;
-  p += z.n1;
-  A.x1 = p;
-  p += z.n1;
-  A.tt1 = p;
-  p += z.n1;
-  A.gt1 = p;
-  p += z.ngt1;
-  double* BA = p;
-  p += z.nba;
-  double* partial = p;
-  p += 2 * MR_EBLOCKS;
-  double* e_dev = p;
+  auto take = [&p](size_t bytes) {
+    double* q = p;
+    p += mr_dbl(bytes);
+    return q;
+  };
+  double* nu = take(8 * (size_t)z.n4);
+  A.tp = take(8 * (size_t)z.n4);
+  A.xp = take(8 * (size_t)z.n4);
+  A.z1 = take(8 * (size_t)z.n4);
+  A.z2 = take(8 * (size_t)z.n4a);
+  A.z3 = take(8 * (size_t)z.n4a);
+  A.g2t = take(8 * (size_t)z.ng2t);
+  A.w3 = take(8 * (size_t)z.nw3);
+  A.t1 = take(8 * (size_t)z.n1);
+  A.x1 = take(8 * (size_t)z.n1);
+  A.tt1 = take(8 * (size_t)z.n1);
+  A.gt1 = take(8 * (size_t)z.ngt1);
+  double* BA = take(8 * (size_t)z.nba);
+  double* partial = take(8 * (2 * (size_t)MR_EBLOCKS + 16));
+  double* e_dev = partial + 2 * MR_EBLOCKS;
   A.nu = nu;
   A.tpp = nu;  // nu is consumed by the amplitude stage before tpp is formed
 
@@ -151,8 +157,26 @@ int mr_energy_rest(const Geometry& g, const double* B, const double* eps, const 
     DSRG_PHASE("phase_mr_integrals", st);
     mr_gather_active_kernel<<<(unsigned)ceil_div(z.nba, MR_NT), MR_NT, 0, st>>>(z.nba, g.nh, g.np, g.na, B, BA);
     DSRG_LAUNCH_CHECK();
-    DSRG_TRY(gemm_f64(g.nh * g.np, g.nh * g.na, g.nq, 1.0, B, (long)g.nh * g.np, false, BA, (long)g.nh * g.na,
-                      false, 0.0, nu, (long)g.nh * g.na, 1, 0, 0, 0, st));
+    const int M = g.nh * g.np, N = g.nh * g.na;
+    if (mr_tensor_gemm(g, ks)) {
+      // rows (i, a) of B and (j, y) of BA, contraction over Q: exact digit planes
+      const int kp = pad64(g.nq);
+      __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)ks * M * kp));
+      __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)ks * N * kp));
+      int* ea = reinterpret_cast<int*>(take(4 * (size_t)(M + N)));
+      int* eb = ea + M;
+      int* err = reinterpret_cast<int*>(take(32));
+      DSRG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+      DSRG_TRY(slice_rows(ks, B, M, g.nq, 1, M, kp, pa, ea, st));
+      DSRG_TRY(slice_rows(ks, BA, N, g.nq, 1, N, kp, pb, eb, st));
+      DSRG_TRY(sliced_plain_gemm(ks, M, N, pa, ea, pb, eb, kp, nu, N, err, st));
+      int h = 0;
+      DSRG_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      DSRG_CUDA(cudaStreamSynchronize(st));
+      if (h) return DSRG_FNO_ERR_TIMEOUT;
+    } else {
+      DSRG_TRY(gemm_f64(M, N, g.nq, 1.0, B, M, false, BA, N, false, 0.0, nu, N, 1, 0, 0, 0, st));
+    }
   }
   DSRG_PHASE("phase_mr_terms", st);
   DSRG_TRY(launch_elems(mr_amp_kernel, A, z.n4, st));

@@ -184,9 +184,11 @@ int check_finite(const double* x, long n, int* flag, cudaStream_t st);
 bool is_device_ptr(const void* p);
 
 // Full multi-reference PT2 energy beyond E_vv, float64 (energy_mr.cu).
-size_t mr_energy_work_doubles(const Geometry& g);
-int mr_energy_rest(const Geometry& g, const double* B, const double* eps, const double* f_hp, const double* g1,
-                   const double* l2, const double* l3, double* work, double* e_out, cudaStream_t st);
+// ks > 0: the integral GEMM on the digit-plane tensor-core path with ks planes (naux >= SLICED_MIN_K).
+size_t mr_energy_work_doubles(const Geometry& g, int ks);
+int mr_energy_rest(const Geometry& g, int ks, const double* B, const double* eps, const double* f_hp,
+                   const double* g1, const double* l2, const double* l3, double* work, double* e_out,
+                   cudaStream_t st);
 
 // Single-instance pipeline stages on an explicit workspace (abi.cu); the C
 // entry points call them on the per-device workspace, the batch runner on
