@@ -119,3 +119,33 @@ def test_full_energy_rejects_bad_arguments():
     # the workspace stays usable after the rejected calls
     e, _ = pkg.dsrg_fno_pt2_energy_mr(gp)
     assert abs(e - O.pt2_energy(p)) <= 1e-8
+
+
+def test_full_energy_nvir1200_properties():
+    """The benchmark's nvir 1200 / naux 3600 CAS(10,10) workload, fast form,
+    where the dense oracle does not fit in memory: its E_vv part against the
+    stored oracle value, and the full energy unchanged (to the fast form's
+    tolerance) by an orthogonal transformation of the auxiliary index (pairs
+    of functions rotated by seeded angles, then permuted), which leaves every
+    integral sum_Q B^Q B^Q unchanged in exact arithmetic."""
+    import json
+    import os
+    name = "sa_cas10_ncore60_nvir1200_naux3600"
+    ref = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name + ".json")))
+    p = workload(name)
+    l3 = cuda(random_cumulant3(p.nact, 2))
+    e, evv = pkg.dsrg_fno_pt2_energy_mr(pkg.problem_from_synth(p, "cuda", pkg.SLICED_BF16), l3)
+    print(f"E2 {e:.9f} E_vv {evv:.9f} stored E_vv {ref['e2']:.9f}")
+    assert abs(evv - ref["e2"]) <= 1e-7
+    assert abs(e - evv) > 1e-3 * abs(e)
+    rng = np.random.default_rng(7)
+    th = rng.uniform(0.0, 2.0 * np.pi, p.naux // 2)[:, None, None]
+    B = p.B
+    B2 = np.empty_like(B)
+    B2[0::2] = np.cos(th) * B[0::2] - np.sin(th) * B[1::2]
+    B2[1::2] = np.sin(th) * B[0::2] + np.cos(th) * B[1::2]
+    p.B = np.ascontiguousarray(B2[rng.permutation(p.naux)])
+    del B, B2
+    e_rot, evv_rot = pkg.dsrg_fno_pt2_energy_mr(pkg.problem_from_synth(p, "cuda", pkg.SLICED_BF16), l3)
+    print(f"rotated: E2 {e_rot:.9f} (diff {e_rot - e:+.2e}), E_vv diff {evv_rot - evv:+.2e}")
+    assert abs(e_rot - e) <= 1e-7 and abs(evv_rot - evv) <= 1e-7
