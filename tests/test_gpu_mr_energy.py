@@ -3,8 +3,9 @@ every amplitude class, and Eq. 11's correction with it, on the GPU (C ABI)
 against the FP64 oracle.
 
 Tolerances (the spec bar for energies): |dE| <= 1e-8 E_h in the
-float64 form, 1e-7 E_h in the digit-plane form (whose E_vv part runs on the
-tensor cores; the rest is float64 in both); the same N'.  Sizes span
+float64 form, 1e-7 E_h in the digit-plane form (whose E_vv part and, for
+naux >= 256, the integrals of the rest run on the tensor cores; the rest's
+element stages are float64 in both); the same N'.  Sizes span
 several GEMM tiles with ragged tails, no core, no active orbitals (singles
 of f_hp only), with and without the 3-cumulant.
 """
