@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from synth import make_problem
+from synth import make_problem, random_cumulant3
 from fockspace import TinySystem, so
 
 
@@ -798,3 +798,32 @@ def test_full_correction_limits():
     r.eps = p.eps[: p.ncore + p.nact + k]
     r.f_hp = p.f_hp[:, : p.nact + k]
     assert abs(efk - O.pt2_energy(r)) <= 1e-12 * abs(efk)
+
+
+def test_full_pt2_energy_invariances_and_s_limit():
+    """E^(2) over every class is unchanged by an orthogonal rotation of the
+    auxiliary index, by a permutation of the virtuals (with their energies and
+    Fock columns) and by sign flips of virtual orbitals (their B and f
+    columns), and vanishes at s = 0 (every amplitude does)."""
+    p = make_problem(3, 4, 10, 24, seed=31, nstates=2)
+    rng = np.random.default_rng(31)
+    p.f_hp = 0.05 * rng.standard_normal((p.nh, p.np_))
+    l3 = random_cumulant3(p.nact, 31)
+    e = O.pt2_energy(p, l3)
+    from copy import copy
+    q = copy(p)
+    Q, _ = np.linalg.qr(rng.standard_normal((p.naux, p.naux)))
+    q.B = np.einsum("PQ,Qhp->Php", Q, p.B)
+    assert abs(O.pt2_energy(q, l3) - e) <= 1e-12 * abs(e)
+    r = copy(p)
+    perm = rng.permutation(p.nvir)
+    sign = rng.choice([-1.0, 1.0], p.nvir)
+    cols = np.concatenate([np.arange(p.nact), p.nact + perm])
+    scale = np.concatenate([np.ones(p.nact), sign])
+    r.B = p.B[:, :, cols] * scale
+    r.f_hp = p.f_hp[:, cols] * scale
+    r.eps = np.concatenate([p.eps[: p.nh], p.eps[p.nh:][perm]])
+    assert abs(O.pt2_energy(r, l3) - e) <= 1e-12 * abs(e)
+    z = copy(p)
+    z.s = 0.0
+    assert O.pt2_energy(z, l3) == 0.0
