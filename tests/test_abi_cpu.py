@@ -116,3 +116,33 @@ def test_eig_batch_rejects_bad_arguments_before_any_work():
     assert lib.dsrg_fno_debug_eig_batch(1, dims(5000), arr, arr) == -1
     assert lib.dsrg_fno_debug_eig_batch(1, dims(2), nul, arr) == -1
     assert lib.dsrg_fno_debug_eig_batch(1, None, arr, arr) == -1
+
+
+def test_full_energy_calls_reject_bad_arguments_before_any_work():
+    """dsrg_fno_pt2_energy_mr and dsrg_fno_discarded_correction_mr check their
+    arguments on the host: a null problem, host (not device) arrays in the
+    problem, and a null output return DSRG_FNO_ERR_ARG without device work."""
+    import numpy as np
+
+    import paper_2312_07008_gb300 as pkg
+    from paper_2312_07008_gb300.binding import CProblem
+    lib = pkg.load()
+    e, ev = ctypes.c_double(7.0), ctypes.c_double(7.0)
+    assert lib.dsrg_fno_pt2_energy_mr(None, None, ctypes.byref(e), ctypes.byref(ev), None) == -1
+    nc, na, nv, nq = 2, 2, 3, 4
+    B = np.zeros((nq, nc + na, na + nv))
+    eps = np.zeros(nc + na + nv)
+    g1 = np.eye(na)
+    l2 = np.zeros((na,) * 4)
+    w = (ctypes.c_double * 1)(1.0)
+    vp = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    c = CProblem(nc, na, nv, nq, vp(B), vp(eps), vp(g1), vp(l2), None, 1, w, 0.5, 0, 0)
+    assert lib.dsrg_fno_pt2_energy_mr(ctypes.byref(c), None, ctypes.byref(e), None, None) == -1
+    assert lib.dsrg_fno_pt2_energy_mr(ctypes.byref(c), None, None, None, None) == -1
+    no = np.eye(nv)
+    de = ctypes.c_double(7.0)
+    assert lib.dsrg_fno_discarded_correction_mr(None, None, 1, vp(no), None, ctypes.byref(de), None, None,
+                                                None) == -1
+    assert lib.dsrg_fno_discarded_correction_mr(ctypes.byref(c), None, 1, vp(no), None, ctypes.byref(de), None,
+                                                None, None) == -1
+    assert e.value == 7.0 and ev.value == 7.0 and de.value == 7.0
